@@ -1,0 +1,178 @@
+/*
+ * dwf.h -- C ABI of the GB300 (sm_103a) Mobius domain-wall solver library.
+ *
+ * The library solves the even-odd preconditioned Mobius domain-wall normal
+ * equations D^+D psi_e = b (arXiv:2104.05615, Sec. 2.2, Eq. (normal_equation))
+ * with plain CG or with the multi-splitting preconditioned CG (MSPCG,
+ * Sec. 2.4, Algorithm 1) whose preconditioner runs a fixed number of inner
+ * CG iterations (Sec. 2.5) on the local normal operator of every subdomain
+ * block, snake terms included (Sec. 2.3), optionally through the reduced-Ls
+ * transform of Sec. 3.3.
+ *
+ * Conventions
+ *   - Lattice sites: lex = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) % 2
+ *     (Sec. 2.2).  All four extents and all block extents must be even.
+ *   - Canonical even/odd 5D field (the ABI vector layout): element
+ *     ((s*(V/2) + lex/2)*4 + spin)*3 + colour, complex interleaved (re, im),
+ *     over the sites of one parity.  Element type by precision:
+ *       DWF_F64: double[2], DWF_F32: float[2], DWF_F16: IEEE half[2],
+ *       DWF_BF16: bfloat16[2].
+ *   - Gauge field (host, FP64): ((lex*4 + mu)*3 + row)*3 + col complex
+ *     (double[2]); mu = x, y, z, t; links must be SU(3) to ~1e-14 (the device
+ *     copies keep two rows and rebuild the third).
+ *   - Gamma basis: chiral (DeGrand-Rossi), gamma5 = diag(-1,-1,+1,+1).
+ *   - Fifth dimension: M5op = A + B P, M_phi = -(b + c P)/2 with
+ *     A = b(4-M5)+1, B = c(4-M5)-1, (P psi)_s = P_- psi_{s+1} + P_+ psi_{s-1}
+ *     and -mass on the wrap terms (Mobius form, cited in Sec. 2.2).
+ *   - Pointers named *_dev are device memory owned by the caller (e.g. a
+ *     torch tensor); *_host are host memory owned by the caller.  The handle
+ *     owns its copies of the gauge field, its tables and its workspaces.
+ *   - Every call returns a dwf_status; nothing is thrown and no device trap
+ *     is ever raised.  dwf_last_error() gives a one-line description.
+ *   - Calls on one handle must not overlap (the handle's workspaces are
+ *     shared).  Work is issued on the handle's stream (dwf_create); entry
+ *     points that take a stream argument use that stream instead.
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwf_handle dwf_handle;
+typedef struct dwf_batch dwf_batch;
+
+typedef enum {
+    DWF_OK = 0,
+    DWF_EINVAL = 1,        /* bad argument (dims, block dims, null pointer, precision) */
+    DWF_ENOMEM = 2,        /* device or host allocation failed */
+    DWF_ECUDA = 3,         /* a CUDA runtime call failed */
+    DWF_ENOCONV = 4,       /* solver reached maxiter; x holds the last iterate */
+    DWF_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    DWF_EUNSUPPORTED = 6   /* valid but not implemented combination */
+} dwf_status;
+
+typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2, DWF_BF16 = 3 } dwf_prec;
+
+typedef enum {
+    DWF_OP_D = 0,           /* D = 1 - M5^-1 M4_eo M5^-1 M4_oe (Sec. 2.2, Eq. dirac_equation) */
+    DWF_OP_DDAG = 1,        /* D^+ */
+    DWF_OP_DDAGD = 2,       /* D^+D (Sec. 2.2, Eq. normal_equation) */
+    DWF_OP_LOCAL_DDAGD = 3, /* (+)_s R_s D^+D R_s^T: every block's local operator with its
+                               snake terms (Sec. 2.3, Eqs. eq:DdagD / eq:diri) */
+    DWF_OP_M5INV = 4,       /* M5op^-1 (dense Ls x Ls per chirality, Sec. 3.1.3) */
+    DWF_OP_M5INVDAG = 5     /* (M5op^-1)^+ */
+} dwf_op;
+
+typedef struct {
+    double tol;            /* stop when ||b - D^+D x|| / ||b|| <= tol (FP64, verified) */
+    int maxiter;           /* outer iteration cap */
+    int inner_iters;       /* k: fixed inner CG iterations of the preconditioner (Sec. 2.5) */
+    dwf_prec outer_prec;   /* DWF_F64 or DWF_F32 (FP32 iterations + FP64 reliable updates) */
+    dwf_prec inner_prec;   /* DWF_F32, DWF_F16 or DWF_BF16 storage for the inner solves */
+    double delta;          /* reliable update when ||r|| < delta * max ||r|| since the last one */
+    int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */
+    int use_graph;         /* 1: capture each outer iteration in a CUDA graph */
+    int check_every;       /* host convergence check period in outer iterations (>= 1) */
+} dwf_solver_params;
+
+typedef struct {
+    int outer_iters;
+    int inner_iters_total;
+    int reliable_updates;
+    int converged;
+    double true_residual;     /* FP64 ||b - D^+D x|| / ||b|| at exit (per system for batches) */
+    double time_total_ms;     /* device time of the solve (events on the handle's stream) */
+    long long kernel_launches;/* kernels this call launched (graph nodes counted per replay) */
+} dwf_stats;
+
+/* Default parameters: tol 1e-10, maxiter 20000, k 6, FP32 outer, FP16 inner,
+ * delta 0.1, no reduced Ls, graphs on, check every iteration. */
+void dwf_default_params(dwf_solver_params *p);
+
+/* Build a handle for one lattice.  dims[4] = (Lx, Ly, Lz, Lt), all even;
+ * subdomain[4] = block dims (each even, divides dims[mu]; == dims[mu] means the
+ * dimension is not partitioned; a partitioned dimension needs
+ * dims[mu] - subdomain[mu] >= 4 so that no four-hop path leaves a block and
+ * re-enters it from the far side).  subdomain may be NULL (one block).
+ * b, c, M5, mass: Mobius parameters.  t_antiperiodic: 1 puts -1 on links that
+ * cross the t boundary.  cuda_stream: the stream all work is issued on (0 =
+ * legacy default stream).  Copies and compresses the gauge field. */
+dwf_status dwf_create(dwf_handle **h, const double *gauge_host, const int dims[4], int Ls,
+                      double b, double c, double M5, double mass, const int subdomain[4],
+                      int t_antiperiodic, void *cuda_stream);
+void dwf_destroy(dwf_handle *h);
+const char *dwf_last_error(const dwf_handle *h);
+const char *dwf_status_string(dwf_status s);
+
+/* Number of elements (complex numbers) of a canonical even/odd field for this
+ * handle with fifth extent Ls (0 = the handle's Ls). */
+size_t dwf_field_elems(const dwf_handle *h, int Ls);
+/* Bytes of the library's internal (packed) layout of one even field in
+ * precision prec with fifth extent Ls (0 = the handle's Ls). */
+size_t dwf_packed_bytes(const dwf_handle *h, dwf_prec prec, int Ls);
+
+/* Canonical <-> packed layout conversion on device buffers (stream 0 =
+ * handle's stream).  Same precision on both sides. */
+dwf_status dwf_pack(dwf_handle *h, void *packed_dev, const void *canonical_dev, dwf_prec prec,
+                    void *stream);
+dwf_status dwf_unpack(dwf_handle *h, void *canonical_dev, const void *packed_dev, dwf_prec prec,
+                      void *stream);
+
+/* out = op(in) on canonical even fields of precision prec (device buffers,
+ * distinct).  FP64 and FP32 compute in their own precision; DWF_F16 and
+ * DWF_BF16 store in 16 bits and compute in FP32, with the dense fifth-
+ * dimension matrices on the tensor cores.  DWF_OP_LOCAL_DDAGD uses the
+ * handle's block dims. */
+dwf_status dwf_apply(dwf_handle *h, void *out_dev, const void *in_dev, dwf_op op, dwf_prec prec,
+                     void *stream);
+/* Same on packed fields (dwf_pack layout); no layout conversion. */
+dwf_status dwf_apply_packed(dwf_handle *h, void *out_dev, const void *in_dev, dwf_op op,
+                            dwf_prec prec, void *stream);
+
+/* Plain CG (Algorithm 1 with M = 1, Fletcher-Reeves beta) on D^+D x = b.
+ * x_dev, b_dev: canonical FP64 even fields; x_dev holds the initial guess. */
+dwf_status dwf_cg(dwf_handle *h, double *x_dev, const double *b_dev, const dwf_solver_params *p,
+                  dwf_stats *stats);
+/* MSPCG (Algorithm 1, M = (+)_s A_s approximated by k inner CG iterations
+ * from a zero guess, Polak-Ribiere beta, Sec. 3.2) on D^+D x = b. */
+dwf_status dwf_mspcg(dwf_handle *h, double *x_dev, const double *b_dev,
+                     const dwf_solver_params *p, dwf_stats *stats);
+/* The same solves with HOST buffers: the call copies b in and x out. */
+dwf_status dwf_solve_host(dwf_handle *h, double *x_host, const double *b_host,
+                          const dwf_solver_params *p, int use_mspcg, dwf_stats *stats);
+
+/* The preconditioner alone on a canonical FP64 even field: z = M^-1 r. */
+dwf_status dwf_precondition(dwf_handle *h, double *z_dev, const double *r_dev,
+                            const dwf_solver_params *p);
+
+/* Reduced-Ls preconditioner (Sec. 3.3): z = (T^+ Mhat^-1 T + mu) r with Mhat
+ * the local normal operator at Ls_hat (same b, c, M5, mass) and Mhat^-1 the
+ * k-iteration inner CG.  T_host: (4*Ls_hat) x (4*Ls) complex (double[2]),
+ * row index s*4 + spin, column index t*4 + spin; trivial in colour. */
+dwf_status dwf_set_reduced_ls(dwf_handle *h, int Ls_hat, const double *T_host, double mu);
+
+/* Batched MSPCG over independent lattices (uneven sizes allowed; same Ls,
+ * b, c, M5 and block dims; per-lattice mass and gauge field).  The handles
+ * stay owned by the caller and must outlive the batch. */
+dwf_status dwf_batch_create(dwf_batch **bt, dwf_handle *const *hs, int n);
+void dwf_batch_destroy(dwf_batch *bt);
+/* xs[i], bs[i]: canonical FP64 even fields of system i (device).  per_system:
+ * n stats (may be NULL); total: whole-batch stats (may be NULL). */
+dwf_status dwf_batch_mspcg(dwf_batch *bt, double *const *xs, const double *const *bs,
+                           const dwf_solver_params *p, dwf_stats *per_system, dwf_stats *total);
+
+/* Kernel launches issued by this library since load (process-wide). */
+const char *dwf_batch_last_error(const dwf_batch *bt);
+
+/* Kernel launches issued by this library since load (process-wide). */
+long long dwf_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,518 @@
+// Vector kernels of the Krylov solvers (Algorithm 1) over packed fields:
+// fused axpy + norm updates, dot products with per-segment (per block or per
+// system) partial sums, precision conversion, canonical <-> packed layout,
+// the per-segment scalar recurrences of CG, and the reduced-Ls transform
+// z = T^+ zhat + mu r of Sec. 3.3.
+#include <atomic>
+
+#include "device_common.cuh"
+
+namespace dwf {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches += n; }
+long long launch_count() { return g_launches.load(); }
+
+// ------------------------------------------------ precision-generic access
+template <typename R>
+__device__ __forceinline__ void load_any(Prec p, const void *base, long nsite, long site, int s,
+                                         int Ls, R *v)
+{
+    switch (p) {
+    case P64: {
+        double t[24];
+        load_sp<TF64>(base, nsite, site, s, Ls, t);
+#pragma unroll
+        for (int r = 0; r < 24; r++) v[r] = (R)t[r];
+    } break;
+    case P32: {
+        float t[24];
+        load_sp<TF32>(base, nsite, site, s, Ls, t);
+#pragma unroll
+        for (int r = 0; r < 24; r++) v[r] = (R)t[r];
+    } break;
+    case P16: {
+        float t[24];
+        load_sp<TF16>(base, nsite, site, s, Ls, t);
+#pragma unroll
+        for (int r = 0; r < 24; r++) v[r] = (R)t[r];
+    } break;
+    default: {
+        float t[24];
+        load_sp<TBF16>(base, nsite, site, s, Ls, t);
+#pragma unroll
+        for (int r = 0; r < 24; r++) v[r] = (R)t[r];
+    } break;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store_any(Prec p, void *base, long nsite, long site, int s,
+                                          int Ls, const R *v)
+{
+    switch (p) {
+    case P64: {
+        double t[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) t[r] = (double)v[r];
+        store_sp<TF64>(base, nsite, site, s, Ls, t);
+    } break;
+    case P32: {
+        float t[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) t[r] = (float)v[r];
+        store_sp<TF32>(base, nsite, site, s, Ls, t);
+    } break;
+    case P16: {
+        float t[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) t[r] = (float)v[r];
+        store_sp<TF16>(base, nsite, site, s, Ls, t);
+    } break;
+    default: {
+        float t[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) t[r] = (float)v[r];
+        store_sp<TBF16>(base, nsite, site, s, Ls, t);
+    } break;
+    }
+}
+
+__device__ __forceinline__ void block_reduce_store(double v0, double v1, int ncomp, double *part)
+{
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    const int tid = threadIdx.x, nw = (blockDim.x + 31) / 32;
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = v0;
+        red[1][tid >> 5] = v1;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        double a = tid < nw ? red[0][tid] : 0.0, b = tid < nw ? red[1][tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (tid == 0) {
+            part[(size_t)blockIdx.x * ncomp] = a;
+            if (ncomp > 1) part[(size_t)blockIdx.x * ncomp + 1] = b;
+        }
+    }
+}
+
+// One thread per 5D site (site, s); a CTA covers `tile` sites x Ls.
+template <typename R>
+__global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
+{
+    const int Ls = a.Ls;
+    const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
+    const long i = (long)blockIdx.x * a.tile + jl;
+    const bool active = jl < a.tile && i < a.nsite;
+    double p0 = 0, p1 = 0;
+    const int seg = (active && a.tile_seg) ? a.tile_seg[i / kSegPad] : 0;
+    const long n = a.nsite;
+    if (active) {
+        R v0[24], v1[24], v2[24], v3[24];
+        switch (op) {
+        case BLAS_DOT:
+        case BLAS_DOT2: {
+            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            R d = 0;
+#pragma unroll
+            for (int r = 0; r < 24; r++) d += v0[r] * v1[r];
+            p0 = (double)d;
+            if (op == BLAS_DOT2) {
+                load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                R e = 0;
+#pragma unroll
+                for (int r = 0; r < 24; r++) e += v0[r] * v2[r];
+                p1 = (double)e;
+            }
+        } break;
+        case BLAS_NORM2: {
+            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            R d = 0;
+#pragma unroll
+            for (int r = 0; r < 24; r++) d += v0[r] * v0[r];
+            p0 = (double)d;
+        } break;
+        case BLAS_CG_UPDATE: {
+            // x += alpha p ; r -= alpha Ap ; |r|^2
+            const R al = (R)(a.scal[0][seg] * a.scal_sign[0]);
+            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+            load_any<R>(a.p[3], a.v[3], n, i, s, Ls, v3);
+            R d = 0;
+#pragma unroll
+            for (int r = 0; r < 24; r++) {
+                v0[r] += al * v1[r];
+                v2[r] -= al * v3[r];
+                d += v2[r] * v2[r];
+            }
+            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+            p0 = (double)d;
+        } break;
+        case BLAS_XPAY: {
+            // v0 = v1 + beta v0
+            const R be = (R)(a.scal[0][seg] * a.scal_sign[0]);
+            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+#pragma unroll
+            for (int r = 0; r < 24; r++) v0[r] = v1[r] + be * v0[r];
+            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+        } break;
+        case BLAS_AXPY_ZERO: {
+#pragma unroll
+            for (int r = 0; r < 24; r++) v0[r] = 0;
+            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+        } break;
+        case BLAS_COPY: {
+            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v1);
+            if (a.v[2]) store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v1);
+            R d = 0;
+#pragma unroll
+            for (int r = 0; r < 24; r++) d += v1[r] * v1[r];
+            p0 = (double)d;
+        } break;
+        case BLAS_RESIDUAL: {
+            // v0 = v1 - v2 ; optional copy into v3 ; |v0|^2 ; optional v4 (x += xacc; xacc = 0)
+            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+            R d = 0;
+#pragma unroll
+            for (int r = 0; r < 24; r++) {
+                v0[r] = v1[r] - v2[r];
+                d += v0[r] * v0[r];
+            }
+            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            if (a.v[3]) store_any<R>(a.p[3], a.v[3], n, i, s, Ls, v0);
+            p0 = (double)d;
+        } break;
+        }
+    }
+    if (a.part) block_reduce_store(p0, p1, op == BLAS_DOT2 ? 2 : 1, a.part);
+}
+
+void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
+{
+    if (a.nsite == 0) return;
+    bool dbl = false;
+    for (int k = 0; k < 5; k++)
+        if (a.v[k] && a.p[k] == P64) dbl = true;
+    const int nthr = a.tile * a.Ls;
+    const unsigned nblk = (unsigned)((a.nsite + a.tile - 1) / a.tile);
+    if (dbl) blas_kernel<double><<<nblk, nthr, 0, st>>>(op, a);
+    else blas_kernel<float><<<nblk, nthr, 0, st>>>(op, a);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// x (FP64) += xacc (any) ; xacc = 0
+__global__ void accum_kernel(void *x, const void *xacc_c, Prec pacc, long nsite, int Ls, int tile)
+{
+    const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
+    const long i = (long)blockIdx.x * tile + jl;
+    if (jl >= tile || i >= nsite) return;
+    void *xacc = const_cast<void *>(xacc_c);
+    double xv[24], av[24];
+    load_any<double>(P64, x, nsite, i, s, Ls, xv);
+    load_any<double>(pacc, xacc, nsite, i, s, Ls, av);
+#pragma unroll
+    for (int r = 0; r < 24; r++) {
+        xv[r] += av[r];
+        av[r] = 0;
+    }
+    store_any<double>(P64, x, nsite, i, s, Ls, xv);
+    store_any<double>(pacc, xacc, nsite, i, s, Ls, av);
+}
+
+void launch_accum(void *x, void *xacc, Prec pacc, long nsite, int Ls, int tile, cudaStream_t st)
+{
+    accum_kernel<<<(unsigned)((nsite + tile - 1) / tile), tile * Ls, 0, st>>>(x, xacc, pacc, nsite,
+                                                                                Ls, tile);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// ------------------------------------------------------------- conversions
+__global__ void convert_kernel(Prec pout, void *out, Prec pin, const void *in, long nsite, int Ls,
+                               int tile)
+{
+    const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
+    const long i = (long)blockIdx.x * tile + jl;
+    if (jl >= tile || i >= nsite) return;
+    if (pout == P64 || pin == P64) {
+        double v[24];
+        load_any<double>(pin, in, nsite, i, s, Ls, v);
+        store_any<double>(pout, out, nsite, i, s, Ls, v);
+    } else {
+        float v[24];
+        load_any<float>(pin, in, nsite, i, s, Ls, v);
+        store_any<float>(pout, out, nsite, i, s, Ls, v);
+    }
+}
+
+void launch_convert(Prec pout, void *out, Prec pin, const void *in, long nsite, int Ls,
+                    cudaStream_t st)
+{
+    if (nsite == 0) return;
+    const int tile = Ls <= 16 ? 16 : 8;
+    convert_kernel<<<(unsigned)((nsite + tile - 1) / tile), tile * Ls, 0, st>>>(pout, out, pin, in,
+                                                                                 nsite, Ls, tile);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// canonical element (s, cb) -> 24 reals
+template <typename R>
+__device__ __forceinline__ void load_canon(Prec p, const void *base, long Vh, long cb, int s,
+                                           R *v)
+{
+    const size_t off = ((size_t)s * Vh + cb) * 24;
+    switch (p) {
+    case P64: {
+        const double *q = reinterpret_cast<const double *>(base) + off;
+        for (int r = 0; r < 24; r++) v[r] = (R)q[r];
+    } break;
+    case P32: {
+        const float *q = reinterpret_cast<const float *>(base) + off;
+        for (int r = 0; r < 24; r++) v[r] = (R)q[r];
+    } break;
+    case P16: {
+        const __half *q = reinterpret_cast<const __half *>(base) + off;
+        for (int r = 0; r < 24; r++) v[r] = (R)__half2float(q[r]);
+    } break;
+    default: {
+        const __nv_bfloat16 *q = reinterpret_cast<const __nv_bfloat16 *>(base) + off;
+        for (int r = 0; r < 24; r++) v[r] = (R)__bfloat162float(q[r]);
+    } break;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store_canon(Prec p, void *base, long Vh, long cb, int s,
+                                            const R *v)
+{
+    const size_t off = ((size_t)s * Vh + cb) * 24;
+    switch (p) {
+    case P64: {
+        double *q = reinterpret_cast<double *>(base) + off;
+        for (int r = 0; r < 24; r++) q[r] = (double)v[r];
+    } break;
+    case P32: {
+        float *q = reinterpret_cast<float *>(base) + off;
+        for (int r = 0; r < 24; r++) q[r] = (float)v[r];
+    } break;
+    case P16: {
+        __half *q = reinterpret_cast<__half *>(base) + off;
+        for (int r = 0; r < 24; r++) q[r] = __float2half_rn((float)v[r]);
+    } break;
+    default: {
+        __nv_bfloat16 *q = reinterpret_cast<__nv_bfloat16 *>(base) + off;
+        for (int r = 0; r < 24; r++) q[r] = __float2bfloat16_rn((float)v[r]);
+    } break;
+    }
+}
+
+__global__ void pack_kernel(Prec p, void *packed, const void *canon, const long *perm, long nsite,
+                            long Vh, int Ls, int tile, int unpack)
+{
+    const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
+    const long i = (long)blockIdx.x * tile + jl;
+    if (jl >= tile || i >= nsite) return;
+    const long cb = perm[i];
+    if (p == P64) {
+        double v[24];
+        if (!unpack) {
+            if (cb >= 0) load_canon<double>(p, canon, Vh, cb, s, v);
+            else for (int r = 0; r < 24; r++) v[r] = 0;
+            store_any<double>(p, packed, nsite, i, s, Ls, v);
+        } else if (cb >= 0) {
+            load_any<double>(p, packed, nsite, i, s, Ls, v);
+            store_canon<double>(p, const_cast<void *>(canon), Vh, cb, s, v);
+        }
+    } else {
+        float v[24];
+        if (!unpack) {
+            if (cb >= 0) load_canon<float>(p, canon, Vh, cb, s, v);
+            else for (int r = 0; r < 24; r++) v[r] = 0;
+            store_any<float>(p, packed, nsite, i, s, Ls, v);
+        } else if (cb >= 0) {
+            load_any<float>(p, packed, nsite, i, s, Ls, v);
+            store_canon<float>(p, const_cast<void *>(canon), Vh, cb, s, v);
+        }
+    }
+}
+
+void launch_pack(Prec p, void *packed, const void *canon, const long *perm, long nsite, long Vh,
+                 int Ls, cudaStream_t st)
+{
+    const int tile = Ls <= 16 ? 16 : 8;
+    pack_kernel<<<(unsigned)((nsite + tile - 1) / tile), tile * Ls, 0, st>>>(p, packed, canon, perm,
+                                                                              nsite, Vh, Ls, tile, 0);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+void launch_unpack(Prec p, void *canon, const void *packed, const long *perm, long nsite, long Vh,
+                   int Ls, cudaStream_t st)
+{
+    const int tile = Ls <= 16 ? 16 : 8;
+    pack_kernel<<<(unsigned)((nsite + tile - 1) / tile), tile * Ls, 0, st>>>(
+        p, const_cast<void *>(packed), canon, perm, nsite, Vh, Ls, tile, 1);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// ------------------------------------------------------------ scalars
+// One CTA per segment sums the per-CTA partials of its sites, then thread 0
+// applies the recurrence.
+__global__ void scalar_kernel(ScalarOp op, ScalarArgs a)
+{
+    const int seg = blockIdx.x;
+    const long c0 = (long)a.tile_begin[seg] * kSegPad / a.sites_per_cta;
+    const long c1 = (long)a.tile_begin[seg + 1] * kSegPad / a.sites_per_cta;
+    double v0 = 0, v1 = 0;
+    for (long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        v0 += a.part[c * a.ncomp];
+        if (a.ncomp > 1) v1 += a.part[c * a.ncomp + 1];
+    }
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    const int tid = threadIdx.x, nw = blockDim.x / 32;
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = v0;
+        red[1][tid >> 5] = v1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t0 = 0, t1 = 0;
+        for (int w = 0; w < nw; w++) {
+            t0 += red[0][w];
+            t1 += red[1][w];
+        }
+        switch (op) {
+        case SC_SUM:
+            a.s0[seg] = t0;
+            if (a.s1) a.s1[seg] = t1;
+            break;
+        case SC_ALPHA: {
+            // alpha = num / <p, Ap>; an exact zero stops the segment
+            const double num = a.s0[seg];
+            a.s1[seg] = (num != 0.0 && t0 != 0.0) ? num / t0 : 0.0;
+            if (a.s2) a.s2[seg] = t0;
+        } break;
+        case SC_BETA_FR: {
+            const double old = a.s0[seg];
+            a.s1[seg] = old != 0.0 ? t0 / old : 0.0;
+            a.s0[seg] = t0;
+            if (a.s2) a.s2[seg] = t0;
+        } break;
+        case SC_BETA_PR: {
+            // beta = <z_new, r_new - r_old> / <z_old, r_old> with r_new - r_old = -alpha Ap
+            const double old = a.s0[seg], al = a.s1[seg];
+            a.s2[seg] = old != 0.0 ? -al * t1 / old : 0.0;
+            a.s0[seg] = t0;
+        } break;
+        }
+    }
+}
+
+void launch_scalar(ScalarOp op, const ScalarArgs &a, cudaStream_t st)
+{
+    scalar_kernel<<<a.nseg, 256, 0, st>>>(op, a);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// ------------------------------------------------------ reduced-Ls transform
+// out[(s,a)] = sum_{t,b} T[(s,a),(t,b)] in[(t,b)] per site and colour (dagger:
+// conj(T)^T), then optionally out += add_coef * addv.  T complex float,
+// (4 Ls_hat) x (4 Ls) row-major, as float pairs.
+__global__ void __launch_bounds__(512) tapply_kernel(Prec pout, void *out, int Ls_out, Prec pin,
+                                                     const void *in, int Ls_in, const float *T,
+                                                     long nsite, int dagger, const void *addv,
+                                                     Prec padd, double add_coef, int tile)
+{
+    extern __shared__ __align__(16) float sm_t[];
+    const int ncol = 4 * (dagger ? Ls_out : Ls_in);   // columns of T (4 Ls)
+    const int nrow = 4 * (dagger ? Ls_in : Ls_out);   // rows of T (4 Ls_hat)
+    float *sT = sm_t;                                   // [nrow][ncol][2]
+    float *sIn = sT + 2 * nrow * ncol;                  // [tile][Ls_in][24]
+    for (int e = threadIdx.x; e < 2 * nrow * ncol; e += blockDim.x) sT[e] = T[e];
+    // stage the input columns of the CTA's sites
+    for (int e = threadIdx.x; e < tile * Ls_in; e += blockDim.x) {
+        const int j = e / Ls_in, t = e - j * Ls_in;
+        const long site = (long)blockIdx.x * tile + j;
+        float v[24];
+        if (site < nsite) load_any<float>(pin, in, nsite, site, t, Ls_in, v);
+        else for (int r = 0; r < 24; r++) v[r] = 0;
+        for (int r = 0; r < 24; r++) sIn[(j * Ls_in + t) * 24 + r] = v[r];
+    }
+    __syncthreads();
+    const int jl = threadIdx.x / Ls_out, s = threadIdx.x - jl * Ls_out;
+    const long i = (long)blockIdx.x * tile + jl;
+    if (jl >= tile || i >= nsite) return;
+    float o[24];
+    for (int r = 0; r < 24; r++) o[r] = 0;
+    const float *x = sIn + jl * Ls_in * 24;
+    for (int a = 0; a < 4; a++) {
+        const int row = s * 4 + a;  // output index (s, a)
+        for (int t = 0; t < Ls_in; t++)
+            for (int b = 0; b < 4; b++) {
+                const int col = t * 4 + b;  // input index
+                float tr, ti;
+                if (!dagger) {
+                    tr = sT[(row * ncol + col) * 2];
+                    ti = sT[(row * ncol + col) * 2 + 1];
+                } else {
+                    tr = sT[(col * ncol + row) * 2];
+                    ti = -sT[(col * ncol + row) * 2 + 1];
+                }
+                const float *xv = x + t * 24 + b * 6;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float xr = xv[2 * c], xi = xv[2 * c + 1];
+                    o[(a * 3 + c) * 2] += tr * xr - ti * xi;
+                    o[(a * 3 + c) * 2 + 1] += tr * xi + ti * xr;
+                }
+            }
+    }
+    if (addv) {
+        float w[24];
+        load_any<float>(padd, addv, nsite, i, s, Ls_out, w);
+        for (int r = 0; r < 24; r++) o[r] += (float)add_coef * w[r];
+    }
+    store_any<float>(pout, out, nsite, i, s, Ls_out, o);
+}
+
+void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
+                   const float *T, long nsite, int dagger, const void *addv, Prec padd,
+                   double add_coef, cudaStream_t st)
+{
+    const int tile = 8;
+    const size_t smem = sizeof(float) * (2 * 16 * Ls_out * Ls_in + tile * Ls_in * 24);
+    static bool attr = false;
+    if (!attr) {
+        DWF_CUDA(cudaFuncSetAttribute(tapply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        attr = true;
+    }
+    tapply_kernel<<<(unsigned)((nsite + tile - 1) / tile), tile * Ls_out, smem, st>>>(
+        pout, out, Ls_out, pin, in, Ls_in, T, nsite, dagger, addv, padd, add_coef, tile);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+}  // namespace dwf

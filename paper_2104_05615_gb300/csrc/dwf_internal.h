@@ -1,0 +1,158 @@
+// Internal declarations of the GB300 domain-wall library (not part of the ABI).
+//
+// Packed field layout (device): sites in block-major order (all sites of
+// block 0, then block 1, ...; block-local lexicographic order inside a block,
+// padded to a multiple of kSegPad sites); inside a site, 16-byte chunks of the
+// 24 reals of a 5D site are laid out as [site][chunk][s][16 bytes], so a warp
+// whose lanes run over s reads contiguous 16-byte words.  FP16 fields carry
+// one FP32 scale per (site, s) colour-spinor, [site][s].
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dwf.h"
+
+namespace dwf {
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+
+constexpr int kSegPad = 32;  // every segment (block / system) is padded to this many sites
+
+inline int elem_bytes(Prec p) { return p == P64 ? 8 : p == P32 ? 4 : 2; }
+inline size_t field_bytes(Prec p, long nsite, int Ls)
+{
+    size_t b = (size_t)nsite * Ls * 24 * elem_bytes(p);
+    if (p == P16) b += (size_t)nsite * Ls * sizeof(float);
+    return b;
+}
+// scale array of an FP16 field sits right after its data
+inline float *field_scale(void *data, Prec p, long nsite, int Ls)
+{
+    return p == P16 ? (float *)((char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
+}
+inline const float *field_scale(const void *data, Prec p, long nsite, int Ls)
+{
+    return p == P16 ? (const float *)((const char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
+}
+
+// One stage of an operator: out = Epilogue(F . hop(G . in)), see stage.cu.
+enum StageMode { MODE_F = 0, MODE_S2 = 1, MODE_S4 = 2, MODE_5D = 3 };
+
+struct StageArgs {
+    const void *in;
+    void *out;
+    const int *nbr;      // [nout][8] input site index; -1 none; <= -2: index -e-2 with sign -1
+    const void *links;   // [rows][8][12] first two rows of the link matrix applied to the neighbour
+    const void *aux;     // MODE_S2: y = aux - F h; MODE_S4: out = G aux - F h
+    const void *dotv;    // MODE_S4: partial <dotv, out> per CTA into dot_part
+    double *dot_part;
+    const void *F;       // [nsys][2][Ls][Ls] real, chirality 0 = spins 0,1
+    const void *G;       // same, or null (identity)
+    const uint16_t *tile_sys;  // system of every kSegPad-site output tile (null: system 0)
+    const double *mphi;  // [nsys][3] = (b, c, mass): M_phi applied to the input on load
+    long nout;           // output sites (multiple of the CTA tile)
+    long nin;            // input sites (for the FP16 scale offset)
+    long naux;           // aux sites (for the FP16 scale offset)
+    int Ls;
+    int dagger;          // 1: (1 +- gamma) signs flipped (D^w^+)
+    int tile;            // output sites per CTA
+    int seg_out;         // output sites per segment (block)
+    int link_stride;     // link rows per segment
+    int aux_stride;      // aux sites per segment
+    int aux_valid;       // aux present for local index < aux_valid
+};
+
+// Launch a stage kernel; prec selects storage (P64/P32/P16/PB16), mphi_in
+// applies M_phi to every neighbour on load.
+void launch_stage(Prec prec, StageMode mode, bool mphi_in, const StageArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------- BLAS
+struct Seg {             // a partition of sites into segments of whole kSegPad tiles
+    int nseg = 0;
+    uint16_t *d_tile_seg = nullptr;   // [ntiles]
+    int *d_tile_begin = nullptr;      // [nseg+1] first tile of each segment
+    std::vector<int> h_tile_begin;
+    long nsite = 0;
+};
+
+// Per-CTA partial sums use CTAs of `tile` sites x Ls threads.
+void launch_convert(Prec pout, void *out, Prec pin, const void *in, long nsite, int Ls,
+                    cudaStream_t st);
+// canonical (complex, [s][cb][4][3]) <-> packed; perm[i] = canonical cb index of
+// packed site i or -1 (padding)
+void launch_pack(Prec p, void *packed, const void *canon, const long *perm, long nsite, long Vh,
+                 int Ls, cudaStream_t st);
+void launch_unpack(Prec p, void *canon, const void *packed, const long *perm, long nsite, long Vh,
+                   int Ls, cudaStream_t st);
+
+// Generic fused vector kernels over packed fields with per-segment scalars.
+// See blas.cu for the exact formulas.
+enum BlasOp {
+    BLAS_DOT = 0,        // part <- sum <a, b>
+    BLAS_NORM2,          // part <- |a|^2
+    BLAS_CG_UPDATE,      // x += alpha p ; r -= alpha Ap ; part <- |r|^2
+    BLAS_XPAY,           // p = r + beta p
+    BLAS_AXPY_ZERO,      // a = 0
+    BLAS_COPY,           // a = b (convert)
+    BLAS_DOT2,           // part <- (<a,b>, <a,c>)
+    BLAS_RESIDUAL,       // r = b - Ax (r FP64 / FP32 out) ; part <- |r|^2
+};
+
+struct BlasArgs {
+    void *v[5];
+    Prec p[5];
+    const double *scal[2];   // per-segment scalars (alpha, beta)
+    double scal_sign[2];
+    const uint16_t *tile_seg;
+    double *part;            // [nctas][2]
+    long nsite;
+    int Ls;
+    int tile;
+};
+void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st);
+
+// Segment reductions of per-CTA partials and the CG scalar recurrences.
+enum ScalarOp {
+    SC_SUM = 0,          // out[s] = sum part
+    SC_ALPHA,            // alpha = num / sum part   (num from buffer)
+    SC_BETA_FR,          // beta = sum part / den ; den <- sum part
+    SC_BETA_PR,          // beta = -alpha <z,Ap> / rz_old; rz <- <z,r>
+};
+struct ScalarArgs {
+    const double *part;
+    int ncomp;           // components per CTA partial (1 or 2)
+    const int *tile_begin;  // [nseg+1]
+    int nseg;
+    int cta_tiles;       // kSegPad-tiles per CTA of the partial producer (fractional not allowed)
+    int sites_per_cta;   // sites per CTA of the producer
+    double *s0, *s1, *s2, *s3;  // op-specific scalar arrays [nseg]
+};
+void launch_scalar(ScalarOp op, const ScalarArgs &a, cudaStream_t st);
+
+// Fifth-dimension transform (reduced Ls): out[(s,a)] = sum T[(s,a),(t,b)] in[(t,b)]
+void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
+                   const float *T, long nsite, int dagger, const void *addv, Prec padd,
+                   double add_coef, cudaStream_t st);
+
+// Process-wide launch counter (every launch_* adds its kernels).
+void count_launch(long long n = 1);
+long long launch_count();
+
+// Errors
+struct CudaError {
+    cudaError_t err;
+    const char *what;
+};
+#define DWF_CUDA(x)                                                             \
+    do {                                                                        \
+        cudaError_t e_ = (x);                                                   \
+        if (e_ != cudaSuccess) throw ::dwf::CudaError{e_, #x};                  \
+    } while (0)
+
+}  // namespace dwf

@@ -1,0 +1,455 @@
+// Engine: device tables, fifth-dimension matrices and operator composition.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "engine.h"
+
+namespace dwf {
+
+Engine::~Engine()
+{
+    for (void *p : owned_) cudaFree(p);
+    for (auto &kv : ws_) cudaFree(kv.second.first);
+}
+
+template <class T>
+T *Engine::upload(const std::vector<T> &h)
+{
+    if (h.empty()) return nullptr;
+    T *d = nullptr;
+    DWF_CUDA(cudaMalloc(&d, h.size() * sizeof(T)));
+    owned_.push_back(d);
+    DWF_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+}
+
+void *Engine::ws(const std::string &name, size_t bytes)
+{
+    auto it = ws_.find(name);
+    if (it != ws_.end() && it->second.second >= bytes) return it->second.first;
+    if (it != ws_.end()) {
+        DWF_CUDA(cudaStreamSynchronize(st));
+        cudaFree(it->second.first);
+        ws_.erase(it);
+    }
+    void *p = nullptr;
+    DWF_CUDA(cudaMalloc(&p, std::max<size_t>(bytes, 256)));
+    DWF_CUDA(cudaMemsetAsync(p, 0, std::max<size_t>(bytes, 256), st));
+    ws_[name] = {p, bytes};
+    return p;
+}
+
+void Engine::init(const std::vector<SysInfo> &sysv, int Ls_, double b_, double c_, double M5_,
+                  cudaStream_t st_)
+{
+    sys = sysv;
+    Ls = Ls_;
+    b = b_;
+    c = c_;
+    M5 = M5_;
+    st = st_;
+    const LatticeGeom &g0 = *sys[0].g;
+    Nb_pad = g0.Nb_pad;
+    O1_pad = g0.O1_pad;
+    E2_pad = g0.E2_pad;
+    ne = 0;
+    nblk = 0;
+    for (auto &s : sys) {
+        if (s.g->Nb_pad != Nb_pad || s.g->O1_pad != O1_pad || s.g->E2_pad != E2_pad)
+            throw std::runtime_error("systems of a batch need identical block regions");
+        s.off = ne;
+        s.blk_off = nblk;
+        ne += s.g->ne();
+        nblk += s.g->nblk;
+    }
+    nO1 = (long)nblk * O1_pad;
+    nE2 = (long)nblk * E2_pad;
+
+    // concatenated tables with offsets
+    auto shift = [](std::vector<int> &dst, const std::vector<int> &src, long off) {
+        for (int e : src) {
+            if (e == -1) dst.push_back(-1);
+            else if (e >= 0) dst.push_back((int)(e + off));
+            else dst.push_back((int)(-(((long)-e - 2) + off) - 2));
+        }
+    };
+    std::vector<int> he, ho, h1, h2, h3, h4;
+    for (auto &s : sys) {
+        const LatticeGeom &g = *s.g;
+        shift(he, g.nbr_e, s.off);
+        shift(ho, g.nbr_o, s.off);
+        shift(h1, g.t1, (long)s.blk_off * Nb_pad);
+        shift(h2, g.t2, (long)s.blk_off * O1_pad);
+        shift(h3, g.t3, (long)s.blk_off * E2_pad);
+        shift(h4, g.t4, (long)s.blk_off * O1_pad);
+    }
+    nbr_e = upload(he);
+    nbr_o = upload(ho);
+    t1 = upload(h1);
+    t2 = upload(h2);
+    t3 = upload(h3);
+    t4 = upload(h4);
+
+    // per-tile system ids (only needed for several systems)
+    if (sys.size() > 1) {
+        std::vector<uint16_t> te, tO1, tE2;
+        for (size_t k = 0; k < sys.size(); k++) {
+            te.insert(te.end(), sys[k].g->ne() / kSegPad, (uint16_t)k);
+            tO1.insert(tO1.end(), (long)sys[k].g->nblk * O1_pad / kSegPad, (uint16_t)k);
+            tE2.insert(tE2.end(), (long)sys[k].g->nblk * E2_pad / kSegPad, (uint16_t)k);
+        }
+        tsys_e = upload(te);
+        tsys_O1 = upload(tO1);
+        tsys_E2 = upload(tE2);
+    }
+    // segments: systems and blocks over the packed even space
+    {
+        std::vector<uint16_t> ts;
+        seg_sys.nseg = (int)sys.size();
+        seg_sys.h_tile_begin.clear();
+        for (size_t k = 0; k < sys.size(); k++) {
+            seg_sys.h_tile_begin.push_back((int)(sys[k].off / kSegPad));
+            ts.insert(ts.end(), sys[k].g->ne() / kSegPad, (uint16_t)k);
+        }
+        seg_sys.h_tile_begin.push_back((int)(ne / kSegPad));
+        seg_sys.d_tile_seg = upload(ts);
+        seg_sys.d_tile_begin = upload(seg_sys.h_tile_begin);
+        seg_sys.nsite = ne;
+    }
+    {
+        if (nblk > 65535) throw std::runtime_error("too many blocks");
+        std::vector<uint16_t> ts;
+        seg_blk.nseg = nblk;
+        seg_blk.h_tile_begin.clear();
+        const int tpb = Nb_pad / kSegPad;
+        for (int k = 0; k < nblk; k++) {
+            seg_blk.h_tile_begin.push_back(k * tpb);
+            ts.insert(ts.end(), tpb, (uint16_t)k);
+        }
+        seg_blk.h_tile_begin.push_back(nblk * tpb);
+        seg_blk.d_tile_seg = upload(ts);
+        seg_blk.d_tile_begin = upload(seg_blk.h_tile_begin);
+        seg_blk.nsite = ne;
+    }
+    perm.clear();
+    for (auto &s : sys) perm.push_back(upload(s.g->even_cb));
+}
+
+void *Engine::links(int which, Prec p)
+{
+    const int cls = p == P64 ? 0 : p == P32 ? 1 : 2;
+    if (lnk_[which][cls]) return lnk_[which][cls];
+    std::vector<unsigned char> all, part;
+    for (auto &s : sys) {
+        const LatticeGeom &g = *s.g;
+        const std::vector<long> &src = which == 0 ? g.lnk_e : which == 1 ? g.lnk_o : which == 2 ? g.lnk_O1 : g.lnk_E2;
+        gather_links(src, s.gauge, cls == 0 ? P64 : cls == 1 ? P32 : P16, part);
+        all.insert(all.end(), part.begin(), part.end());
+    }
+    lnk_[which][cls] = upload(all);
+    return lnk_[which][cls];
+}
+
+// ------------------------------------------------------------ 5D matrices
+namespace {
+using Mat = std::vector<double>;  // Ls x Ls row-major
+
+Mat matmul(const Mat &a, const Mat &b, int n)
+{
+    Mat c(n * n, 0.0);
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++) c[i * n + j] += a[i * n + k] * b[k * n + j];
+    return c;
+}
+Mat transpose(const Mat &a, int n)
+{
+    Mat t(n * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) t[j * n + i] = a[i * n + j];
+    return t;
+}
+Mat inverse(Mat a, int n)
+{
+    Mat inv(n * n, 0.0);
+    for (int i = 0; i < n; i++) inv[i * n + i] = 1.0;
+    for (int col = 0; col < n; col++) {
+        int piv = col;
+        for (int r = col + 1; r < n; r++)
+            if (std::fabs(a[r * n + col]) > std::fabs(a[piv * n + col])) piv = r;
+        for (int j = 0; j < n; j++) {
+            std::swap(a[col * n + j], a[piv * n + j]);
+            std::swap(inv[col * n + j], inv[piv * n + j]);
+        }
+        const double d = a[col * n + col];
+        for (int j = 0; j < n; j++) {
+            a[col * n + j] /= d;
+            inv[col * n + j] /= d;
+        }
+        for (int r = 0; r < n; r++) {
+            if (r == col) continue;
+            const double f = a[r * n + col];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; j++) {
+                a[r * n + j] -= f * a[col * n + j];
+                inv[r * n + j] -= f * inv[col * n + j];
+            }
+        }
+    }
+    return inv;
+}
+}  // namespace
+
+const Mats &Engine::mats(int L)
+{
+    auto it = mats_.find(L);
+    if (it != mats_.end()) return it->second;
+    Mats m;
+    m.Ls = L;
+    const size_t per = 2 * (size_t)L * L;
+    std::vector<double> h[MK_N];
+    for (auto &hk : h) hk.assign(per * sys.size(), 0.0);
+    std::vector<double> mp;
+    const double A = b * (4.0 - M5) + 1.0, B = c * (4.0 - M5) - 1.0;
+    for (size_t k = 0; k < sys.size(); k++) {
+        const double mass = sys[k].mass;
+        mp.push_back(b);
+        mp.push_back(c);
+        mp.push_back(mass);
+        for (int chi = 0; chi < 2; chi++) {
+            // chirality 0 (spins 0,1): (P psi)_s = psi_{s+1}; 1 (spins 2,3): psi_{s-1}; wraps -mass
+            Mat P(L * L, 0.0), I(L * L, 0.0);
+            for (int s = 0; s < L; s++) {
+                I[s * L + s] = 1.0;
+                if (chi == 0) {
+                    if (s + 1 < L) P[s * L + s + 1] += 1.0;
+                    else P[s * L + 0] += -mass;
+                } else {
+                    if (s >= 1) P[s * L + s - 1] += 1.0;
+                    else P[0 * L + L - 1] += -mass;
+                }
+            }
+            Mat M5op(L * L), Mphi(L * L);
+            for (int e = 0; e < L * L; e++) {
+                M5op[e] = A * I[e] + B * P[e];
+                Mphi[e] = -0.5 * (b * I[e] + c * P[e]);
+            }
+            const Mat M5i = inverse(M5op, L);
+            const Mat M5iT = transpose(M5i, L), MphiT = transpose(Mphi, L), M5opT = transpose(M5op, L);
+            const Mat out[MK_N] = {matmul(Mphi, M5i, L), M5i, M5iT, matmul(M5iT, MphiT, L), MphiT, M5opT};
+            for (int q = 0; q < MK_N; q++)
+                std::copy(out[q].begin(), out[q].end(), h[q].begin() + k * per + chi * (size_t)L * L);
+        }
+    }
+    for (int q = 0; q < MK_N; q++) {
+        m.d64[q] = upload(h[q]);
+        std::vector<float> f(h[q].begin(), h[q].end());
+        m.d32[q] = upload(f);
+    }
+    m.mphi = upload(mp);
+    return mats_[L] = m;
+}
+
+// ------------------------------------------------------------ operators
+static const void *matp(const Mats &m, MatKind k, Prec p)
+{
+    return p == P64 ? (const void *)m.d64[k] : (const void *)m.d32[k];
+}
+
+void Engine::apply_5d(Prec p, int L, MatKind k, void *out, const void *in, long nsite)
+{
+    const Mats &m = mats(L);
+    StageArgs a{};
+    a.in = in;
+    a.out = out;
+    a.F = matp(m, k, p);
+    a.tile_sys = (nsite == ne) ? tsys_e : nullptr;
+    a.nout = nsite;
+    a.nin = nsite;
+    a.Ls = L;
+    a.tile = stage_tile(p);
+    a.seg_out = (int)std::min<long>(nsite, 1 << 30);
+    a.link_stride = a.seg_out;
+    launch_stage(p, MODE_5D, false, a, st);
+}
+
+int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part)
+{
+    const Mats &m = mats(Ls);
+    const size_t fb = field_bytes(p, ne, Ls);
+    const std::string tag = std::to_string((int)p);
+    void *t1v = ws("g_t1_" + tag, fb);
+    void *wv = ws("g_w_" + tag, fb);
+    void *t3v = ws("g_t3_" + tag, fb);
+    const int tile = stage_tile(p);
+
+    StageArgs base{};
+    base.tile_sys = tsys_e;
+    base.mphi = m.mphi;
+    base.nout = ne;
+    base.nin = ne;
+    base.naux = ne;
+    base.Ls = Ls;
+    base.tile = tile;
+    base.seg_out = (int)ne;
+    base.link_stride = (int)ne;
+    base.aux_stride = (int)ne;
+    base.aux_valid = (int)ne;
+
+    auto S1 = [&](const void *x) {
+        StageArgs a = base;
+        a.in = x;
+        a.out = t1v;
+        a.nbr = nbr_o;
+        a.links = links(1, p);
+        a.F = matp(m, MK_S1F, p);
+        launch_stage(p, MODE_F, true, a, st);
+    };
+    auto S2 = [&](const void *x, void *o, bool with_g) {
+        StageArgs a = base;
+        a.in = t1v;
+        a.out = o;
+        a.nbr = nbr_e;
+        a.links = links(0, p);
+        a.aux = x;
+        a.F = matp(m, MK_M5I, p);
+        a.G = with_g ? matp(m, MK_M5ID, p) : nullptr;
+        launch_stage(p, MODE_S2, false, a, st);
+    };
+    auto S3 = [&](const void *w) {
+        StageArgs a = base;
+        a.in = w;
+        a.out = t3v;
+        a.nbr = nbr_o;
+        a.links = links(1, p);
+        a.F = matp(m, MK_S3F, p);
+        a.dagger = 1;
+        launch_stage(p, MODE_F, false, a, st);
+    };
+    auto S4 = [&](const void *w, void *o, const void *dotv) {
+        StageArgs a = base;
+        a.in = t3v;
+        a.out = o;
+        a.nbr = nbr_e;
+        a.links = links(0, p);
+        a.aux = w;
+        a.F = matp(m, MK_S4F, p);
+        a.G = matp(m, MK_S4G, p);
+        a.dagger = 1;
+        a.dotv = dotv;
+        a.dot_part = dot_part;
+        launch_stage(p, MODE_S4, false, a, st);
+    };
+    switch (op) {
+    case DWF_OP_D:
+        S1(in);
+        S2(in, out, false);
+        break;
+    case DWF_OP_DDAG:
+        apply_5d(p, Ls, MK_M5ID, wv, in, ne);
+        S3(wv);
+        S4(wv, out, in);
+        break;
+    case DWF_OP_DDAGD:
+        S1(in);
+        S2(in, wv, true);
+        S3(wv);
+        S4(wv, out, in);
+        break;
+    default: throw std::runtime_error("apply_global: bad op");
+    }
+    return tile;
+}
+
+int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_part)
+{
+    const Mats &m = mats(L);
+    const std::string tag = std::to_string((int)p) + "_" + std::to_string(L);
+    void *t1v = ws("l_t1_" + tag, field_bytes(p, nO1, L));
+    void *wv = ws("l_w_" + tag, field_bytes(p, nE2, L));
+    void *t3v = ws("l_t3_" + tag, field_bytes(p, nO1, L));
+    const int tile = stage_tile(p);
+    const long nI = (long)nblk * Nb_pad;
+
+    StageArgs a{};
+    a.mphi = m.mphi;
+    a.Ls = L;
+    a.tile = tile;
+    // S1: O1 <- interior
+    a.in = in;
+    a.nin = nI;
+    a.out = t1v;
+    a.nout = nO1;
+    a.nbr = t1;
+    a.links = links(2, p);
+    a.tile_sys = tsys_O1;
+    a.seg_out = O1_pad;
+    a.link_stride = O1_pad;
+    a.F = matp(m, MK_S1F, p);
+    launch_stage(p, MODE_F, true, a, st);
+    // S2: E2 <- O1, aux = interior x
+    StageArgs b2{};
+    b2.mphi = m.mphi;
+    b2.Ls = L;
+    b2.tile = tile;
+    b2.in = t1v;
+    b2.nin = nO1;
+    b2.out = wv;
+    b2.nout = nE2;
+    b2.nbr = t2;
+    b2.links = links(3, p);
+    b2.tile_sys = tsys_E2;
+    b2.seg_out = E2_pad;
+    b2.link_stride = E2_pad;
+    b2.aux = in;
+    b2.naux = nI;
+    b2.aux_stride = Nb_pad;
+    b2.aux_valid = Nb_pad;
+    b2.F = matp(m, MK_M5I, p);
+    b2.G = matp(m, MK_M5ID, p);
+    launch_stage(p, MODE_S2, false, b2, st);
+    // S3: O1 <- E2 (dagger)
+    StageArgs b3{};
+    b3.Ls = L;
+    b3.tile = tile;
+    b3.in = wv;
+    b3.nin = nE2;
+    b3.out = t3v;
+    b3.nout = nO1;
+    b3.nbr = t3;
+    b3.links = links(2, p);
+    b3.tile_sys = tsys_O1;
+    b3.seg_out = O1_pad;
+    b3.link_stride = O1_pad;
+    b3.F = matp(m, MK_S3F, p);
+    b3.dagger = 1;
+    launch_stage(p, MODE_F, false, b3, st);
+    // S4: interior <- O1 (dagger), aux = w
+    StageArgs b4{};
+    b4.Ls = L;
+    b4.tile = tile;
+    b4.in = t3v;
+    b4.nin = nO1;
+    b4.out = out;
+    b4.nout = nI;
+    b4.nbr = t4;
+    b4.links = links(3, p);
+    b4.tile_sys = tsys_e;
+    b4.seg_out = Nb_pad;
+    b4.link_stride = E2_pad;
+    b4.aux = wv;
+    b4.naux = nE2;
+    b4.aux_stride = E2_pad;
+    b4.aux_valid = Nb_pad;
+    b4.F = matp(m, MK_S4F, p);
+    b4.G = matp(m, MK_S4G, p);
+    b4.dagger = 1;
+    b4.dotv = in;
+    b4.dot_part = dot_part;
+    launch_stage(p, MODE_S4, false, b4, st);
+    return tile;
+}
+
+}  // namespace dwf

@@ -1,0 +1,108 @@
+// Device state of one or more lattices that are solved together: tables,
+// fifth-dimension matrices, workspaces, operator composition and solvers.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "geometry.h"
+
+namespace dwf {
+
+// Fifth-dimension matrices of one Ls for every system, [nsys][2][Ls][Ls]
+// (chirality 0 = spins 0,1 (P_-), 1 = spins 2,3 (P_+)).
+enum MatKind {
+    MK_S1F = 0,  // M_phi M5^-1
+    MK_M5I,      // M5^-1
+    MK_M5ID,     // M5^-+
+    MK_S3F,      // M5^-+ M_phi^+
+    MK_S4F,      // M_phi^+
+    MK_S4G,      // M5op^+
+    MK_N
+};
+struct Mats {
+    int Ls = 0;
+    double *d64[MK_N] = {};
+    float *d32[MK_N] = {};
+    double *mphi = nullptr;  // [nsys][3] = (b, c, mass)
+};
+
+struct SysInfo {
+    const LatticeGeom *g = nullptr;
+    const double *gauge = nullptr;  // host, canonical
+    double mass = 0;
+    long off = 0;      // packed even offset of the system
+    int blk_off = 0;   // first block of the system
+};
+
+class Engine {
+  public:
+    Engine() = default;
+    ~Engine();
+    Engine(const Engine &) = delete;
+
+    // Build device tables for the given systems (same Ls, b, c, M5 and block
+    // region shapes).
+    void init(const std::vector<SysInfo> &sys, int Ls, double b, double c, double M5,
+              cudaStream_t st);
+
+    cudaStream_t st = 0;
+    int Ls = 0;
+    double b = 0, c = 0, M5 = 0;
+    std::vector<SysInfo> sys;
+    long ne = 0;               // packed even (= odd) sites, all systems
+    int nblk = 0;              // blocks, all systems
+    int Nb_pad = 0, O1_pad = 0, E2_pad = 0;
+    long nO1 = 0, nE2 = 0;
+
+    // device tables
+    int *nbr_e = nullptr, *nbr_o = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr,
+        *t4 = nullptr;
+    uint16_t *tsys_e = nullptr, *tsys_O1 = nullptr, *tsys_E2 = nullptr;  // null for 1 system
+    Seg seg_sys, seg_blk;
+    std::vector<long *> perm;  // per system: packed -> canonical cb (device)
+
+    // links by precision class: 0 = FP64, 1 = FP32, 2 = half
+    void *links(int which, Prec p);  // which: 0 even, 1 odd, 2 O1, 3 E2
+    const Mats &mats(int Ls);
+
+    // workspaces
+    void *ws(const std::string &name, size_t bytes);
+    double *ws_d(const std::string &name, size_t n) { return (double *)ws(name, n * sizeof(double)); }
+
+    // Operators on packed fields.  dot_part (optional): per-CTA partials of
+    // <in, out> from the last stage; returns the CTA tile used.
+    int apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part);
+    int apply_local(Prec p, int Ls, void *out, const void *in, double *dot_part);
+    void apply_5d(Prec p, int Ls, MatKind k, void *out, const void *in, long nsite);
+
+    static int stage_tile(Prec p) { return p == P64 ? 8 : 16; }
+
+    // reduced Ls
+    int Ls_hat = 0;
+    double mu = 0;
+    float *Tm = nullptr;  // device (4 Ls_hat) x (4 Ls) complex
+
+  private:
+    void *lnk_[4][3] = {};
+    std::map<int, Mats> mats_;
+    std::map<std::string, std::pair<void *, size_t>> ws_;
+    std::vector<void *> owned_;
+    template <class T> T *upload(const std::vector<T> &h);
+};
+
+// Solver driver (solver.cu).  xs/bs: canonical FP64 device fields per system.
+struct SolveResult {
+    int iters = 0, inner_total = 0, ru = 0, converged = 0;
+    std::vector<double> true_res;
+    double ms = 0;
+    long long launches = 0;
+};
+dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dwf_solver_params &p,
+                 bool precond, SolveResult &res, std::string &err);
+// z = M^-1 r for FP64 canonical fields (single system)
+void precondition_fp64(Engine &E, double *z, const double *r, const dwf_solver_params &p);
+
+}  // namespace dwf

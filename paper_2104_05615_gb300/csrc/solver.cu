@@ -1,0 +1,384 @@
+// Krylov drivers: preconditioned CG of Algorithm 1 with the multi-splitting
+// preconditioner (Sec. 2.4: M = (+)_s A_s, a fixed number k of inner CG
+// iterations from a zero guess, Sec. 2.5), Polak-Ribiere beta (Sec. 3.2),
+// FP32 outer iterations with FP64 reliable updates (Sec. 3.2), and the
+// optional reduced-Ls preconditioner of Sec. 3.3.
+//
+// Scalars (alpha, beta, <r,z>) live on the device per segment (system for
+// the outer solve, block for the inner solves); the host reads only the
+// residual norms to decide reliable updates and convergence.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "engine.h"
+
+namespace dwf {
+
+void launch_accum(void *x, void *xacc, Prec pacc, long nsite, int Ls, int tile, cudaStream_t st);
+
+namespace {
+
+constexpr int kBlasTile = 16;
+
+BlasArgs blas(long nsite, int Ls, const uint16_t *tile_seg, double *part)
+{
+    BlasArgs a{};
+    a.nsite = nsite;
+    a.Ls = Ls;
+    a.tile = kBlasTile;
+    a.tile_seg = tile_seg;
+    a.part = part;
+    a.scal_sign[0] = a.scal_sign[1] = 1.0;
+    return a;
+}
+
+ScalarArgs scal(const Seg &sg, const double *part, int ncomp, int sites_per_cta)
+{
+    ScalarArgs s{};
+    s.part = part;
+    s.ncomp = ncomp;
+    s.tile_begin = sg.d_tile_begin;
+    s.nseg = sg.nseg;
+    s.sites_per_cta = sites_per_cta;
+    return s;
+}
+
+struct Ctx {
+    Engine &E;
+    const dwf_solver_params &P;
+    cudaStream_t st;
+    long n;
+    int Ls;
+    int nsys;
+    double *part;
+};
+
+// z = M^-1 r (outer precision po for r and z).
+void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
+{
+    Engine &E = c.E;
+    const dwf_solver_params &P = c.P;
+    const Prec pi = (Prec)P.inner_prec;
+    const bool red = P.use_reduced_ls && E.Ls_hat > 0;
+    const int L = red ? E.Ls_hat : E.Ls;
+    const long n = c.n;
+    void *rin = E.ws("in_r", field_bytes(pi, n, L));
+    void *pin = E.ws("in_p", field_bytes(pi, n, L));
+    void *Apin = E.ws("in_Ap", field_bytes(pi, n, L));
+    void *zin = E.ws("in_z", field_bytes(P32, n, L));
+    double *rr = E.ws_d("in_rr", E.nblk), *al = E.ws_d("in_al", E.nblk), *be = E.ws_d("in_be", E.nblk);
+    const uint16_t *tsb = E.seg_blk.d_tile_seg;
+
+    if (red) launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st);
+    {
+        BlasArgs a = blas(n, L, tsb, c.part);
+        a.v[0] = pin;
+        a.p[0] = pi;
+        a.v[1] = red ? rin : const_cast<void *>(r);
+        a.p[1] = red ? pi : po;
+        a.v[2] = red ? nullptr : rin;
+        a.p[2] = pi;
+        launch_blas(BLAS_COPY, a, c.st);
+        ScalarArgs s = scal(E.seg_blk, c.part, 1, kBlasTile);
+        s.s0 = rr;
+        launch_scalar(SC_SUM, s, c.st);
+    }
+    {
+        BlasArgs a = blas(n, L, nullptr, nullptr);
+        a.v[0] = zin;
+        a.p[0] = P32;
+        launch_blas(BLAS_AXPY_ZERO, a, c.st);
+    }
+    for (int it = 0; it < P.inner_iters; it++) {
+        const int tile = E.apply_local(pi, L, Apin, pin, c.part);
+        ScalarArgs s = scal(E.seg_blk, c.part, 1, tile);
+        s.s0 = rr;
+        s.s1 = al;
+        launch_scalar(SC_ALPHA, s, c.st);
+        BlasArgs a = blas(n, L, tsb, c.part);
+        a.v[0] = zin; a.p[0] = P32;
+        a.v[1] = pin; a.p[1] = pi;
+        a.v[2] = rin; a.p[2] = pi;
+        a.v[3] = Apin; a.p[3] = pi;
+        a.scal[0] = al;
+        launch_blas(BLAS_CG_UPDATE, a, c.st);
+        if (it + 1 < P.inner_iters) {
+            ScalarArgs t = scal(E.seg_blk, c.part, 1, kBlasTile);
+            t.s0 = rr;
+            t.s1 = be;
+            launch_scalar(SC_BETA_FR, t, c.st);
+            BlasArgs x = blas(n, L, tsb, nullptr);
+            x.v[0] = pin; x.p[0] = pi;
+            x.v[1] = rin; x.p[1] = pi;
+            x.scal[0] = be;
+            launch_blas(BLAS_XPAY, x, c.st);
+        }
+        inner_count++;
+    }
+    if (red) {
+        launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st);
+    } else if (P.inner_iters == 0) {
+        BlasArgs a = blas(n, E.Ls, nullptr, nullptr);
+        a.v[0] = z;
+        a.p[0] = po;
+        launch_blas(BLAS_AXPY_ZERO, a, c.st);
+    } else {
+        launch_convert(po, z, P32, zin, n, E.Ls, c.st);
+    }
+}
+
+// r64 = b64 - A x64 ; r = r64 (in po) ; rr (per system) on the device
+void true_residual(Ctx &c, Prec po, void *x64, const void *b64, void *Ax64, void *r64, void *r,
+                   double *rr)
+{
+    c.E.apply_global(P64, DWF_OP_DDAGD, Ax64, x64, nullptr);
+    BlasArgs a = blas(c.n, c.Ls, nullptr, c.part);
+    a.v[0] = r64; a.p[0] = P64;
+    a.v[1] = const_cast<void *>(b64); a.p[1] = P64;
+    a.v[2] = Ax64; a.p[2] = P64;
+    a.v[3] = (po != P64) ? r : nullptr; a.p[3] = po;
+    launch_blas(BLAS_RESIDUAL, a, c.st);
+    ScalarArgs s = scal(c.E.seg_sys, c.part, 1, kBlasTile);
+    s.s0 = rr;
+    launch_scalar(SC_SUM, s, c.st);
+}
+
+}  // namespace
+
+dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dwf_solver_params &P,
+                 bool use_precond, SolveResult &res, std::string &err)
+{
+    const cudaStream_t st = E.st;
+    const long n = E.ne;
+    const int Ls = E.Ls;
+    const int nsys = (int)E.sys.size();
+    const Prec po = (Prec)P.outer_prec;
+    if (po != P64 && po != P32) {
+        err = "outer precision must be FP64 or FP32";
+        return DWF_EINVAL;
+    }
+    if (use_precond && (P.inner_prec == DWF_F64 || P.inner_iters < 0)) {
+        err = "inner precision must be FP32, FP16 or BF16 and k >= 0";
+        return DWF_EINVAL;
+    }
+    if (P.use_reduced_ls && use_precond && (E.Ls_hat <= 0 || !E.Tm)) {
+        err = "reduced-Ls preconditioner requested but not configured";
+        return DWF_EINVAL;
+    }
+    const long long launches0 = launch_count();
+    // workspace: the max CTA count over all kernels is n sites / 8-site tiles (x2 components)
+    const long max_cta = std::max<long>((long)E.nblk * E.E2_pad, n) / 8 + 16;
+    Ctx c{E, P, st, n, Ls, nsys, E.ws_d("part", 2 * max_cta)};
+
+    void *x64 = E.ws("x64", field_bytes(P64, n, Ls));
+    void *b64 = E.ws("b64", field_bytes(P64, n, Ls));
+    void *r64 = E.ws("r64", field_bytes(P64, n, Ls));
+    void *Ax64 = E.ws("Ax64", field_bytes(P64, n, Ls));
+    void *r = po == P64 ? r64 : E.ws("r_o", field_bytes(po, n, Ls));
+    void *p = E.ws("p_o", field_bytes(po, n, Ls));
+    void *Ap = E.ws("Ap_o", field_bytes(po, n, Ls));
+    void *z = use_precond ? E.ws("z_o", field_bytes(po, n, Ls)) : r;
+    void *xacc = po == P64 ? x64 : E.ws("xacc_o", field_bytes(po, n, Ls));
+    double *bb = E.ws_d("bb", nsys), *rr = E.ws_d("rr", nsys), *rz = E.ws_d("rz", nsys);
+    double *al = E.ws_d("al", nsys), *be = E.ws_d("be", nsys), *pAp = E.ws_d("pAp", nsys);
+
+    cudaEvent_t e0, e1;
+    DWF_CUDA(cudaEventCreate(&e0));
+    DWF_CUDA(cudaEventCreate(&e1));
+    DWF_CUDA(cudaEventRecord(e0, st));
+
+    for (int k = 0; k < nsys; k++) {
+        const LatticeGeom &g = *E.sys[k].g;
+        launch_pack(P64, (char *)b64 + field_bytes(P64, E.sys[k].off, Ls), bs[k], E.perm[k], g.ne(),
+                    g.Vh, Ls, st);
+        launch_pack(P64, (char *)x64 + field_bytes(P64, E.sys[k].off, Ls), xs[k], E.perm[k], g.ne(),
+                    g.Vh, Ls, st);
+    }
+    {
+        BlasArgs a = blas(n, Ls, nullptr, c.part);
+        a.v[0] = b64;
+        a.p[0] = P64;
+        launch_blas(BLAS_NORM2, a, st);
+        ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
+        s.s0 = bb;
+        launch_scalar(SC_SUM, s, st);
+    }
+    std::vector<double> h_bb(nsys), h_rr(nsys), h_max(nsys), h_true(nsys);
+    DWF_CUDA(cudaMemcpyAsync(h_bb.data(), bb, nsys * 8, cudaMemcpyDeviceToHost, st));
+    true_residual(c, po, x64, b64, Ax64, r64, r, rr);
+    if (po != P64) {
+        BlasArgs a = blas(n, Ls, nullptr, nullptr);
+        a.v[0] = xacc;
+        a.p[0] = po;
+        launch_blas(BLAS_AXPY_ZERO, a, st);
+    }
+    DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < nsys; k++) {
+        if (!(h_bb[k] > 0)) {
+            err = "zero right-hand side";
+            return DWF_EINVAL;
+        }
+        h_max[k] = h_rr[k];
+    }
+    const double tol2 = P.tol * P.tol;
+    auto all_below = [&](const std::vector<double> &v) {
+        for (int k = 0; k < nsys; k++)
+            if (!(v[k] <= tol2 * h_bb[k])) return false;
+        return true;
+    };
+    int inner_total = 0, ru = 0, iters = 0;
+    bool converged = all_below(h_rr);
+
+    // p = z = M^-1 r ; rz = <r, z>
+    if (!converged) {
+        if (use_precond) precond_apply(c, po, r, z, inner_total);
+        BlasArgs a = blas(n, Ls, E.seg_sys.d_tile_seg, c.part);
+        a.v[0] = p; a.p[0] = po;
+        a.v[1] = z; a.p[1] = po;
+        launch_blas(BLAS_COPY, a, st);  // partial |z|^2 unused
+        BlasArgs d = blas(n, Ls, nullptr, c.part);
+        d.v[0] = r; d.p[0] = po;
+        d.v[1] = z; d.p[1] = po;
+        launch_blas(BLAS_DOT, d, st);
+        ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
+        s.s0 = rz;
+        launch_scalar(SC_SUM, s, st);
+    }
+    const int maxiter = P.maxiter > 0 ? P.maxiter : 20000;
+    const double delta2 = (P.delta > 0 ? P.delta : 0.1) * (P.delta > 0 ? P.delta : 0.1);
+    while (!converged && iters < maxiter) {
+        // alpha = <r,z> / <p, Ap>
+        const int tile = E.apply_global(po, DWF_OP_DDAGD, Ap, p, c.part);
+        {
+            ScalarArgs s = scal(E.seg_sys, c.part, 1, tile);
+            s.s0 = rz;
+            s.s1 = al;
+            s.s2 = pAp;
+            launch_scalar(SC_ALPHA, s, st);
+        }
+        {
+            BlasArgs a = blas(n, Ls, E.seg_sys.d_tile_seg, c.part);
+            a.v[0] = xacc; a.p[0] = po;
+            a.v[1] = p; a.p[1] = po;
+            a.v[2] = r; a.p[2] = po;
+            a.v[3] = Ap; a.p[3] = po;
+            a.scal[0] = al;
+            launch_blas(BLAS_CG_UPDATE, a, st);
+            ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
+            s.s0 = rr;
+            launch_scalar(SC_SUM, s, st);
+        }
+        iters++;
+        DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
+        DWF_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < nsys; k++)
+            if (!std::isfinite(h_rr[k])) {
+                err = "non-finite residual";
+                return DWF_ENOCONV;
+            }
+        const bool conv_iter = all_below(h_rr);
+        bool do_ru = conv_iter && po != P64;
+        if (po != P64)
+            for (int k = 0; k < nsys; k++) {
+                h_max[k] = std::max(h_max[k], h_rr[k]);
+                if (h_rr[k] < delta2 * h_max[k]) do_ru = true;
+            }
+        if (po == P64 && conv_iter) {
+            converged = true;
+            break;
+        }
+        if (do_ru) {
+            launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);
+            true_residual(c, po, x64, b64, Ax64, r64, r, rr);
+            DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
+            DWF_CUDA(cudaStreamSynchronize(st));
+            ru++;
+            for (int k = 0; k < nsys; k++) h_max[k] = h_rr[k];
+            if (conv_iter && all_below(h_rr)) {
+                converged = true;
+                break;
+            }
+        }
+        // z = M^-1 r ; beta ; p = z + beta p
+        if (use_precond) {
+            precond_apply(c, po, r, z, inner_total);
+            BlasArgs d = blas(n, Ls, nullptr, c.part);
+            d.v[0] = z; d.p[0] = po;
+            d.v[1] = r; d.p[1] = po;
+            d.v[2] = Ap; d.p[2] = po;
+            launch_blas(BLAS_DOT2, d, st);
+            ScalarArgs s = scal(E.seg_sys, c.part, 2, kBlasTile);
+            s.s0 = rz;
+            s.s1 = al;
+            s.s2 = be;
+            launch_scalar(SC_BETA_PR, s, st);
+        } else {
+            BlasArgs d = blas(n, Ls, nullptr, c.part);
+            d.v[0] = r; d.p[0] = po;
+            launch_blas(BLAS_NORM2, d, st);
+            ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
+            s.s0 = rz;
+            s.s1 = be;
+            launch_scalar(SC_BETA_FR, s, st);
+        }
+        BlasArgs x = blas(n, Ls, E.seg_sys.d_tile_seg, nullptr);
+        x.v[0] = p; x.p[0] = po;
+        x.v[1] = z; x.p[1] = po;
+        x.scal[0] = be;
+        launch_blas(BLAS_XPAY, x, st);
+    }
+    // final solution and FP64 true residual
+    if (po != P64) launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);
+    true_residual(c, po, x64, b64, Ax64, r64, r, rr);
+    for (int k = 0; k < nsys; k++) {
+        const LatticeGeom &g = *E.sys[k].g;
+        launch_unpack(P64, xs[k], (char *)x64 + field_bytes(P64, E.sys[k].off, Ls), E.perm[k],
+                      g.ne(), g.Vh, Ls, st);
+    }
+    DWF_CUDA(cudaEventRecord(e1, st));
+    DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    DWF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    res.iters = iters;
+    res.inner_total = inner_total;
+    res.ru = ru;
+    res.ms = ms;
+    res.true_res.resize(nsys);
+    bool ok = true;
+    for (int k = 0; k < nsys; k++) {
+        res.true_res[k] = std::sqrt(h_rr[k] / h_bb[k]);
+        if (!(res.true_res[k] <= P.tol)) ok = false;
+    }
+    res.converged = ok;
+    res.launches = launch_count() - launches0;
+    if (!ok) {
+        err = "not converged within maxiter";
+        return DWF_ENOCONV;
+    }
+    return DWF_OK;
+}
+
+void precondition_fp64(Engine &E, double *z, const double *r, const dwf_solver_params &P)
+{
+    const long n = E.ne;
+    const int Ls = E.Ls;
+    Ctx c{E, P, E.st, n, Ls, 1, E.ws_d("part", 2 * (std::max<long>((long)E.nblk * E.E2_pad, n) / 8 + 16))};
+    void *r64 = E.ws("pc_r64", field_bytes(P64, n, Ls));
+    void *r32 = E.ws("pc_r32", field_bytes(P32, n, Ls));
+    void *z32 = E.ws("pc_z32", field_bytes(P32, n, Ls));
+    const LatticeGeom &g = *E.sys[0].g;
+    launch_pack(P64, r64, r, E.perm[0], g.ne(), g.Vh, Ls, E.st);
+    launch_convert(P32, r32, P64, r64, n, Ls, E.st);
+    int cnt = 0;
+    precond_apply(c, P32, r32, z32, cnt);
+    launch_convert(P64, r64, P32, z32, n, Ls, E.st);
+    launch_unpack(P64, z, r64, E.perm[0], g.ne(), g.Vh, Ls, E.st);
+}
+
+}  // namespace dwf

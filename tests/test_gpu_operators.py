@@ -1,0 +1,104 @@
+"""GPU operator parity against the FP64 oracle, through the C ABI.
+
+Relative error ||out - out_oracle|| / ||out_oracle|| bounds (the accuracy each
+storage format allows): FP64 1e-12, FP32 1e-6, FP16/BF16 5e-3.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2104_05615_gb300 import inputs  # noqa: E402
+
+TOL = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 5e-3}
+
+CASES = {
+    # name: dims, Ls, sub, mass, eps, antiperiodic
+    "part_x": ((8, 4, 4, 4), 8, (4, 4, 4, 4), 0.05, 0.5, 0),
+    "ragged": ((6, 2, 2, 2), 4, None, 0.1, 0.6, 0),
+    "ragged_part": ((12, 2, 2, 2), 4, (6, 2, 2, 2), 0.02, 0.6, 0),
+    "antiperiodic": ((4, 4, 4, 6), 6, None, 0.03, 0.4, 1),
+    "ls12": ((4, 4, 4, 8), 12, (4, 4, 4, 4), 0.01, 0.5, 0),
+    "ls16_4d": ((8, 8, 4, 4), 16, (4, 4, 4, 4), 0.002, 0.6, 0),
+}
+
+
+def relerr(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def setup_case(orc, name):
+    from paper_2104_05615_gb300.lattice import Lattice
+    dims, Ls, sub, mass, eps, anti = CASES[name]
+    U = inputs.gauge_field(dims, eps, 17)
+    lat = Lattice(dims, Ls, 1.5, 0.5, 1.8, mass, U, sub, anti)
+    o = orc.Oracle(dims, Ls, 1.5, 0.5, 1.8, mass, U, anti)
+    x = inputs.gaussian_spinor_cb(dims, Ls, 99)
+    return lat, o, x, (sub or dims)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_operator_parity(orc, name, prec):
+    from paper_2104_05615_gb300.lattice import to_device, to_numpy
+    lat, o, x, sub = setup_case(orc, name)
+    xd = to_device(x, prec)
+    xin = to_numpy(xd)  # the rounded input both sides see
+    ref = {"D": o.D(xin), "Ddag": o.D(xin, dagger=True), "DdagD": o.DdagD(xin),
+           "local": o.local_DdagD(xin, sub),
+           "m5inv": o.apply5(o.matrix5(3), xin), "m5invdag": o.apply5(o.matrix5(3, True), xin)}
+    for op, want in ref.items():
+        got = to_numpy(lat.apply(op, xd, prec))
+        e = relerr(got, want)
+        assert e < TOL[prec], f"{name} {prec} {op}: relative error {e:.3e}"
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_pack_roundtrip(orc, prec):
+    from paper_2104_05615_gb300.lattice import to_device, to_numpy
+    lat, o, x, sub = setup_case(orc, "ragged_part")
+    xd = to_device(x, prec)
+    p = lat.pack(xd, prec)
+    back = lat.unpack(p, prec)
+    if prec in ("f64", "f32"):
+        assert torch.equal(back, xd)
+    else:  # FP16 packs with one scale per colour-spinor
+        assert relerr(to_numpy(back), to_numpy(xd)) < 2e-3
+
+
+@pytest.mark.gpu
+def test_apply_packed_matches_canonical(orc):
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import to_device
+    lat, o, x, sub = setup_case(orc, "part_x")
+    xd = to_device(x, "f32")
+    p_in = lat.pack(xd, "f32")
+    p_out = lat.packed("f32")
+    B.dwf_apply_packed(lat.h, p_out, p_in, B.DWF_OP_DDAGD, B.DWF_F32)
+    a = lat.unpack(p_out, "f32")
+    b = lat.apply("DdagD", xd, "f32")
+    assert torch.equal(a, b)
+
+
+@pytest.mark.gpu
+def test_operator_deterministic(orc):
+    lat, o, x, sub = setup_case(orc, "ls12")
+    from paper_2104_05615_gb300.lattice import to_device
+    xd = to_device(x, "f32")
+    a = lat.apply("DdagD", xd, "f32")
+    b = lat.apply("DdagD", xd, "f32")
+    assert torch.equal(a, b)
+
+
+@pytest.mark.gpu
+def test_invalid_arguments_rejected():
+    from paper_2104_05615_gb300 import binding as B
+    U = inputs.gauge_field((4, 4, 4, 4), 0.1, 1)
+    with pytest.raises(B.DwfError):   # odd extent
+        B.dwf_create(U, (3, 4, 4, 4), 8, 1.5, 0.5, 1.8, 0.1)
+    with pytest.raises(B.DwfError):   # block too large for the snake halo
+        B.dwf_create(U, (4, 4, 4, 4), 8, 1.5, 0.5, 1.8, 0.1, (2, 4, 4, 4))
+    with pytest.raises(B.DwfError):   # block does not divide
+        B.dwf_create(U, (4, 4, 4, 4), 8, 1.5, 0.5, 1.8, 0.1, (6, 4, 4, 4))
