@@ -116,6 +116,20 @@ size_t dwf_field_elems(const dwf_handle *h, int Ls);
  * precision prec with fifth extent Ls (0 = the handle's Ls). */
 size_t dwf_packed_bytes(const dwf_handle *h, dwf_prec prec, int Ls);
 
+/* Site counts of the handle's geometry (all counts per parity; "padded"
+ * counts are the device allocation sizes).  Local regions of one block
+ * (Sec. 2.3, snake terms): interior = even sites of the block; o1 = odd sites
+ * within one hop of it; e2 = even sites within two hops. */
+typedef struct {
+    long long even_sites;          /* V/2 */
+    long long even_sites_padded;   /* packed field length in sites */
+    long long blocks;
+    long long block_sites, block_sites_padded;
+    long long o1_sites, o1_sites_padded;
+    long long e2_sites, e2_sites_padded;
+} dwf_geometry;
+dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g);
+
 /* Canonical <-> packed layout conversion on device buffers (stream 0 =
  * handle's stream).  Same precision on both sides. */
 dwf_status dwf_pack(dwf_handle *h, void *packed_dev, const void *canonical_dev, dwf_prec prec,
@@ -166,8 +180,27 @@ void dwf_batch_destroy(dwf_batch *bt);
 dwf_status dwf_batch_mspcg(dwf_batch *bt, double *const *xs, const double *const *bs,
                            const dwf_solver_params *p, dwf_stats *per_system, dwf_stats *total);
 
-/* Kernel launches issued by this library since load (process-wide). */
+/* Last error message of a batch. */
 const char *dwf_batch_last_error(const dwf_batch *bt);
+
+/* Launch configuration of the fused hop-stage kernels of one operator family
+ * (op_kind 0: the global D, D^+, D^+D; 1: the local operator), in one
+ * precision.  tile_sites: output 4D sites per CTA (each CTA holds their whole
+ * Ls-slab); gather: 0 = neighbour spinors loaded by each thread, 1 = bulk
+ * asynchronous copies (TMA engine) of whole neighbour Ls-columns into shared
+ * memory.  By default the first use of an operator in a precision times every
+ * candidate that fits and keeps the fastest (the autotuner, Sec. 3.1.3 tunes
+ * block sizes the same way). */
+typedef struct {
+    int tile_sites;
+    int gather;
+} dwf_kernel_config;
+dwf_status dwf_autotune(dwf_handle *h, dwf_prec prec, int op_kind);
+dwf_status dwf_get_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind, dwf_kernel_config *c);
+/* Fix a configuration (disables autotuning for it).  Rejects choices that do
+ * not fit (shared memory, threads, tile not dividing the segment size). */
+dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
+                                 const dwf_kernel_config *c);
 
 /* Kernel launches issued by this library since load (process-wide). */
 long long dwf_kernel_launch_count(void);

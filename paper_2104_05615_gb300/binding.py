@@ -25,6 +25,19 @@ class dwf_solver_params(C.Structure):
                 ("use_reduced_ls", C.c_int), ("use_graph", C.c_int), ("check_every", C.c_int)]
 
 
+class dwf_geometry(C.Structure):
+    _fields_ = [(n, C.c_longlong) for n in (
+        "even_sites", "even_sites_padded", "blocks", "block_sites", "block_sites_padded",
+        "o1_sites", "o1_sites_padded", "e2_sites", "e2_sites_padded")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class dwf_kernel_config(C.Structure):
+    _fields_ = [("tile_sites", C.c_int), ("gather", C.c_int)]
+
+
 class dwf_stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int),
                 ("reliable_updates", C.c_int), ("converged", C.c_int),
@@ -72,6 +85,10 @@ def lib() -> C.CDLL:
                                     C.POINTER(dwf_stats)]),
             "dwf_batch_last_error": (C.c_char_p, [vp]),
             "dwf_kernel_launch_count": (C.c_longlong, []),
+            "dwf_get_geometry": (i, [vp, C.POINTER(dwf_geometry)]),
+            "dwf_autotune": (i, [vp, i, i]),
+            "dwf_get_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
+            "dwf_set_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -227,6 +244,27 @@ def dwf_batch_mspcg(bt, xs, bs, params=None):
     p = params if params is not None else default_params()
     check(lib().dwf_batch_mspcg(bt, xa, ba, C.byref(p), per, C.byref(tot)), batch=bt)
     return tot, list(per)
+
+
+def dwf_get_geometry(h):
+    g = dwf_geometry()
+    check(lib().dwf_get_geometry(h, C.byref(g)), h)
+    return g.as_dict()
+
+
+def dwf_autotune(h, prec, op_kind):
+    return check(lib().dwf_autotune(h, int(prec), int(op_kind)), h)
+
+
+def dwf_get_kernel_config(h, prec, op_kind):
+    c = dwf_kernel_config()
+    check(lib().dwf_get_kernel_config(h, int(prec), int(op_kind), C.byref(c)), h)
+    return {"tile_sites": c.tile_sites, "gather": c.gather}
+
+
+def dwf_set_kernel_config(h, prec, op_kind, tile_sites, gather):
+    c = dwf_kernel_config(int(tile_sites), int(gather))
+    return check(lib().dwf_set_kernel_config(h, int(prec), int(op_kind), C.byref(c)), h)
 
 
 def dwf_kernel_launch_count():

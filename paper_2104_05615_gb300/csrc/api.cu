@@ -141,6 +141,22 @@ size_t dwf_packed_bytes(const dwf_handle *h, dwf_prec prec, int Ls)
     return field_bytes((Prec)prec, h->E->ne, Ls > 0 ? Ls : h->Ls);
 }
 
+dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g)
+{
+    if (!h || !g) return DWF_EINVAL;
+    const LatticeGeom &G = h->g;
+    g->even_sites = G.Vh;
+    g->even_sites_padded = G.ne();
+    g->blocks = G.nblk;
+    g->block_sites = G.Nb;
+    g->block_sites_padded = G.Nb_pad;
+    g->o1_sites = G.O1;
+    g->o1_sites_padded = G.O1_pad;
+    g->e2_sites = G.E2 - (G.Nb_pad - G.Nb);
+    g->e2_sites_padded = G.E2_pad;
+    return DWF_OK;
+}
+
 static bool prec_ok(int p) { return p >= DWF_F64 && p <= DWF_BF16; }
 
 dwf_status dwf_pack(dwf_handle *h, void *packed, const void *canon, dwf_prec prec, void *stream)
@@ -203,6 +219,10 @@ dwf_status dwf_apply(dwf_handle *h, void *out, const void *in, dwf_op op, dwf_pr
         dwf_status s = apply_packed_impl(h, pout, pin, op, prec);
         if (s != DWF_OK) return s;
         launch_unpack((Prec)prec, out, pout, E.perm[0], h->g.ne(), h->g.Vh, h->Ls, E.st);
+        if (E.check_err()) {
+            h->err = "a bounded device wait gave up";
+            return DWF_ETIMEOUT;
+        }
         return DWF_OK;
     });
 }
@@ -358,6 +378,46 @@ dwf_status dwf_batch_mspcg(dwf_batch *bt, double *const *xs, const double *const
         }
         return s;
     });
+}
+
+static int op_Ls(dwf_handle *h, int op_kind)
+{
+    return (op_kind == 1 && h->E->Ls_hat > 0) ? h->E->Ls : h->Ls;
+}
+
+dwf_status dwf_autotune(dwf_handle *h, dwf_prec prec, int op_kind)
+{
+    if (!h || !prec_ok(prec) || op_kind < 0 || op_kind > 1) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        h->E->autotune((Prec)prec, op_kind, op_Ls(h, op_kind));
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_get_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind, dwf_kernel_config *c)
+{
+    if (!h || !c || !prec_ok(prec) || op_kind < 0 || op_kind > 1) return DWF_EINVAL;
+    const Engine::KCfg &k = h->E->cfg[op_kind][prec];
+    c->tile_sites = k.tile;
+    c->gather = k.gather;
+    return DWF_OK;
+}
+
+dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
+                                 const dwf_kernel_config *c)
+{
+    if (!h || !c || !prec_ok(prec) || op_kind < 0 || op_kind > 1) return DWF_EINVAL;
+    if (c->tile_sites < 2 || c->tile_sites % 2 || (c->gather != 0 && c->gather != 1)) return DWF_EINVAL;
+    const long seg = op_kind == 0 ? h->E->ne : (long)h->E->Nb_pad;
+    if (seg % c->tile_sites || !stage_fits((Prec)prec, c->tile_sites, h->Ls, c->gather)) {
+        h->err = "kernel configuration does not fit";
+        return DWF_EINVAL;
+    }
+    Engine::KCfg &k = h->E->cfg[op_kind][prec];
+    k.tile = c->tile_sites;
+    k.gather = (prec == DWF_F64) ? 0 : c->gather;
+    k.tuned = true;
+    return DWF_OK;
 }
 
 const char *dwf_batch_last_error(const dwf_batch *bt) { return bt ? bt->err.c_str() : "null"; }

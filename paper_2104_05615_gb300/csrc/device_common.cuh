@@ -357,3 +357,101 @@ __device__ __forceinline__ void accumulate(int mu, R sg, R w, const R *chi, R *a
 }
 
 }  // namespace dwf
+
+namespace dwf {
+
+// Compile-time variants of the projector and the rebuild-and-accumulate step:
+// MU the direction, SG = +1 or -1 the sign in (1 + SG gamma_MU).  h is the
+// half spinor, already multiplied by the neighbour's weight.
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void project_ct(const R *p, R w, R *h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const R p0r = p[(0 * 3 + c) * 2], p0i = p[(0 * 3 + c) * 2 + 1];
+        const R p1r = p[(1 * 3 + c) * 2], p1i = p[(1 * 3 + c) * 2 + 1];
+        const R p2r = p[(2 * 3 + c) * 2], p2i = p[(2 * 3 + c) * 2 + 1];
+        const R p3r = p[(3 * 3 + c) * 2], p3i = p[(3 * 3 + c) * 2 + 1];
+        R h0r, h0i, h1r, h1i;
+        if constexpr (MU == 0) {  // h0 = p0 + SG i p3, h1 = p1 + SG i p2
+            h0r = SG > 0 ? p0r - p3i : p0r + p3i;
+            h0i = SG > 0 ? p0i + p3r : p0i - p3r;
+            h1r = SG > 0 ? p1r - p2i : p1r + p2i;
+            h1i = SG > 0 ? p1i + p2r : p1i - p2r;
+        } else if constexpr (MU == 1) {  // h0 = p0 + SG p3, h1 = p1 - SG p2
+            h0r = SG > 0 ? p0r + p3r : p0r - p3r;
+            h0i = SG > 0 ? p0i + p3i : p0i - p3i;
+            h1r = SG > 0 ? p1r - p2r : p1r + p2r;
+            h1i = SG > 0 ? p1i - p2i : p1i + p2i;
+        } else if constexpr (MU == 2) {  // h0 = p0 + SG i p2, h1 = p1 - SG i p3
+            h0r = SG > 0 ? p0r - p2i : p0r + p2i;
+            h0i = SG > 0 ? p0i + p2r : p0i - p2r;
+            h1r = SG > 0 ? p1r + p3i : p1r - p3i;
+            h1i = SG > 0 ? p1i - p3r : p1i + p3r;
+        } else {  // h0 = p0 + SG p2, h1 = p1 + SG p3
+            h0r = SG > 0 ? p0r + p2r : p0r - p2r;
+            h0i = SG > 0 ? p0i + p2i : p0i - p2i;
+            h1r = SG > 0 ? p1r + p3r : p1r - p3r;
+            h1i = SG > 0 ? p1i + p3i : p1i - p3i;
+        }
+        h[(0 * 3 + c) * 2] = w * h0r;
+        h[(0 * 3 + c) * 2 + 1] = w * h0i;
+        h[(1 * 3 + c) * 2] = w * h1r;
+        h[(1 * 3 + c) * 2 + 1] = w * h1i;
+    }
+}
+
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void accumulate_ct(const R *chi, R *acc)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const R c0r = chi[(0 * 3 + c) * 2], c0i = chi[(0 * 3 + c) * 2 + 1];
+        const R c1r = chi[(1 * 3 + c) * 2], c1i = chi[(1 * 3 + c) * 2 + 1];
+        acc[(0 * 3 + c) * 2] += c0r;
+        acc[(0 * 3 + c) * 2 + 1] += c0i;
+        acc[(1 * 3 + c) * 2] += c1r;
+        acc[(1 * 3 + c) * 2 + 1] += c1i;
+        R *a2 = acc + (2 * 3 + c) * 2, *a3 = acc + (3 * 3 + c) * 2;
+        if constexpr (MU == 0) {  // r2 = -SG i c1 ; r3 = -SG i c0   (-i z = (z.i, -z.r))
+            if (SG > 0) { a2[0] += c1i; a2[1] -= c1r; a3[0] += c0i; a3[1] -= c0r; }
+            else        { a2[0] -= c1i; a2[1] += c1r; a3[0] -= c0i; a3[1] += c0r; }
+        } else if constexpr (MU == 1) {  // r2 = -SG c1 ; r3 = SG c0
+            if (SG > 0) { a2[0] -= c1r; a2[1] -= c1i; a3[0] += c0r; a3[1] += c0i; }
+            else        { a2[0] += c1r; a2[1] += c1i; a3[0] -= c0r; a3[1] -= c0i; }
+        } else if constexpr (MU == 2) {  // r2 = -SG i c0 ; r3 = SG i c1
+            if (SG > 0) { a2[0] += c0i; a2[1] -= c0r; a3[0] -= c1i; a3[1] += c1r; }
+            else        { a2[0] -= c0i; a2[1] += c0r; a3[0] += c1i; a3[1] -= c1r; }
+        } else {  // r2 = SG c0 ; r3 = SG c1
+            if (SG > 0) { a2[0] += c0r; a2[1] += c0i; a3[0] += c1r; a3[1] += c1i; }
+            else        { a2[0] -= c0r; a2[1] -= c0i; a3[0] -= c1r; a3[1] -= c1i; }
+        }
+    }
+}
+
+// chi = U h reading U (3x3 complex, 20-real stride) from shared memory.
+template <typename R>
+__device__ __forceinline__ void su3_mul_half_smem(const R *U, const R *h, R *chi)
+{
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        R u[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) u[q] = U[r * 6 + q];
+#pragma unroll
+        for (int sp = 0; sp < 2; sp++) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const R ur = u[2 * c], ui = u[2 * c + 1];
+                const R hr = h[(sp * 3 + c) * 2], hi = h[(sp * 3 + c) * 2 + 1];
+                re += ur * hr - ui * hi;
+                im += ur * hi + ui * hr;
+            }
+            chi[(sp * 3 + r) * 2] = re;
+            chi[(sp * 3 + r) * 2 + 1] = im;
+        }
+    }
+}
+
+}  // namespace dwf

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -55,7 +56,7 @@ struct StageArgs {
     const void *F;       // [nsys][2][Ls][Ls] real, chirality 0 = spins 0,1
     const void *G;       // same, or null (identity)
     const uint16_t *tile_sys;  // system of every kSegPad-site output tile (null: system 0)
-    const double *mphi;  // [nsys][3] = (b, c, mass): M_phi applied to the input on load
+    const double *mphi;  // [nsys][5] = (b, c, mass, A, B): M_phi on load, S4 coefficients
     long nout;           // output sites (multiple of the CTA tile)
     long nin;            // input sites (for the FP16 scale offset)
     long naux;           // aux sites (for the FP16 scale offset)
@@ -66,7 +67,12 @@ struct StageArgs {
     int link_stride;     // link rows per segment
     int aux_stride;      // aux sites per segment
     int aux_valid;       // aux present for local index < aux_valid
+    int *err;            // device flag set when a bounded wait gives up (may be null)
+    int gather;          // 0: direct neighbour loads; 1: bulk-copy staging in shared memory
 };
+
+// Does a (tile, gather) choice fit the per-CTA limits for this precision and Ls?
+bool stage_fits(Prec prec, int tile, int Ls, int gather);
 
 // Launch a stage kernel; prec selects storage (P64/P32/P16/PB16), mphi_in
 // applies M_phi to every neighbour on load.

@@ -4,6 +4,8 @@
 #include <cstring>
 #include <stdexcept>
 
+#include <cuda_fp16.h>
+
 #include "engine.h"
 
 namespace dwf {
@@ -135,6 +137,16 @@ void Engine::init(const std::vector<SysInfo> &sysv, int Ls_, double b_, double c
     }
     perm.clear();
     for (auto &s : sys) perm.push_back(upload(s.g->even_cb));
+    err_flag = upload(std::vector<int>(1, 0));
+}
+
+bool Engine::check_err()
+{
+    int h = 0;
+    DWF_CUDA(cudaMemcpyAsync(&h, err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(cudaStreamSynchronize(st));
+    if (h) DWF_CUDA(cudaMemsetAsync(err_flag, 0, sizeof(int), st));
+    return h != 0;
 }
 
 void *Engine::links(int which, Prec p)
@@ -218,6 +230,8 @@ const Mats &Engine::mats(int L)
         mp.push_back(b);
         mp.push_back(c);
         mp.push_back(mass);
+        mp.push_back(A);
+        mp.push_back(B);
         for (int chi = 0; chi < 2; chi++) {
             // chirality 0 (spins 0,1): (P psi)_s = psi_{s+1}; 1 (spins 2,3): psi_{s-1}; wraps -mass
             Mat P(L * L, 0.0), I(L * L, 0.0);
@@ -238,7 +252,8 @@ const Mats &Engine::mats(int L)
             }
             const Mat M5i = inverse(M5op, L);
             const Mat M5iT = transpose(M5i, L), MphiT = transpose(Mphi, L), M5opT = transpose(M5op, L);
-            const Mat out[MK_N] = {matmul(Mphi, M5i, L), M5i, M5iT, matmul(M5iT, MphiT, L), MphiT, M5opT};
+            const Mat out[MK_N] = {matmul(Mphi, M5i, L), M5i, M5iT, matmul(M5iT, MphiT, L), MphiT,
+                                   M5opT, matmul(M5iT, M5i, L)};
             for (int q = 0; q < MK_N; q++)
                 std::copy(out[q].begin(), out[q].end(), h[q].begin() + k * per + chi * (size_t)L * L);
         }
@@ -247,6 +262,44 @@ const Mats &Engine::mats(int L)
         m.d64[q] = upload(h[q]);
         std::vector<float> f(h[q].begin(), h[q].end());
         m.d32[q] = upload(f);
+    }
+    // tensor-core operand A per kind: k-step 0 and 1 matrices (null = zero)
+    if (L <= 16) {
+        const size_t nsys = sys.size();
+        std::vector<double> ident(per * nsys, 0.0), neg[MK_N];
+        for (size_t k = 0; k < nsys; k++)
+            for (int chi = 0; chi < 2; chi++)
+                for (int s = 0; s < L; s++) ident[k * per + chi * L * L + s * L + s] = 1.0;
+        for (int q = 0; q < MK_N; q++) {
+            neg[q] = h[q];
+            for (double &v : neg[q]) v = -v;
+        }
+        const std::vector<double> *src[TC_N][2] = {
+            {&h[MK_S1F], nullptr},  {&h[MK_M5ID], &neg[MK_S2GF]}, {&ident, &neg[MK_M5I]},
+            {&h[MK_S3F], nullptr},  {&h[MK_S4G], &neg[MK_S4F]},   {&h[MK_M5I], nullptr},
+            {&h[MK_M5ID], nullptr}};
+        for (int q = 0; q < TC_N; q++) {
+            std::vector<__half> frag(nsys * 2 * 2 * 32 * 8, __float2half(0.f));
+            for (size_t k = 0; k < nsys; k++)
+                for (int chi = 0; chi < 2; chi++)
+                    for (int kk = 0; kk < 2; kk++) {
+                        const std::vector<double> *M = src[q][kk];
+                        if (!M) continue;
+                        auto A = [&](int r, int c) -> double {
+                            return (r < L && c < L) ? (*M)[k * per + chi * L * L + r * L + c] : 0.0;
+                        };
+                        for (int lane = 0; lane < 32; lane++) {
+                            const int g = lane >> 2, tg = lane & 3;
+                            const double v[8] = {A(g, 2 * tg),     A(g, 2 * tg + 1),
+                                                 A(g + 8, 2 * tg), A(g + 8, 2 * tg + 1),
+                                                 A(g, 2 * tg + 8), A(g, 2 * tg + 9),
+                                                 A(g + 8, 2 * tg + 8), A(g + 8, 2 * tg + 9)};
+                            __half *dst = frag.data() + ((((k * 2 + chi) * 2 + kk) * 32 + lane) * 8);
+                            for (int e = 0; e < 8; e++) dst[e] = __float2half_rn((float)v[e]);
+                        }
+                    }
+            m.tc[q] = upload(frag);
+        }
     }
     m.mphi = upload(mp);
     return mats_[L] = m;
@@ -258,21 +311,88 @@ static const void *matp(const Mats &m, MatKind k, Prec p)
     return p == P64 ? (const void *)m.d64[k] : (const void *)m.d32[k];
 }
 
+static bool is_half(Prec p) { return p == P16 || p == PB16; }
+
+// Matrices of a stage: CUDA-core path F (and G), tensor-core path the fused
+// operand A; G is kept non-null on the tensor-core path only as a flag.
+static void set_mats(StageArgs &a, const Mats &m, Prec p, MatKind f, MatKind g, TcKind tc)
+{
+    if (is_half(p)) {
+        if (!m.tc[tc]) throw std::runtime_error("tensor-core path needs Ls <= 16");
+        a.F = m.tc[tc];
+        a.G = (g == MK_N) ? nullptr : m.tc[tc];
+    } else {
+        a.F = matp(m, f, p);
+        a.G = (g == MK_N) ? nullptr : matp(m, g, p);
+    }
+}
+
 void Engine::apply_5d(Prec p, int L, MatKind k, void *out, const void *in, long nsite)
 {
     const Mats &m = mats(L);
     StageArgs a{};
+    a.err = err_flag;
     a.in = in;
     a.out = out;
-    a.F = matp(m, k, p);
+    set_mats(a, m, p, k, MK_N, k == MK_M5I ? TC_M5I : TC_M5ID);
     a.tile_sys = (nsite == ne) ? tsys_e : nullptr;
     a.nout = nsite;
     a.nin = nsite;
     a.Ls = L;
-    a.tile = stage_tile(p);
+    a.tile = 8;
     a.seg_out = (int)std::min<long>(nsite, 1 << 30);
     a.link_stride = a.seg_out;
     launch_stage(p, MODE_5D, false, a, st);
+}
+
+const Engine::KCfg &Engine::kcfg(Prec p, int which, int Ls_op)
+{
+    KCfg &c = cfg[which][p];
+    if (!c.tuned && autotune_on) autotune(p, which, Ls_op);
+    return c;
+}
+
+void Engine::autotune(Prec p, int which, int Ls_op, int reps)
+{
+    KCfg &c = cfg[which][p];
+    c.tuned = true;  // also guards the recursion through apply_*
+    c.tile = 8;
+    c.gather = 0;
+    const long n = ne;
+    void *x = ws("tune_x", field_bytes(p, n, Ls_op));
+    void *y = ws("tune_y", field_bytes(p, n, Ls_op));
+    cudaEvent_t e0, e1;
+    DWF_CUDA(cudaEventCreate(&e0));
+    DWF_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    KCfg bestc = c;
+    const int tiles[] = {4, 8, 16, 32};
+    for (int gather = 0; gather < (p == P64 ? 1 : 2); gather++)
+        for (int tile : tiles) {
+            if (!stage_fits(p, tile, Ls_op, gather)) continue;
+            if ((which == 0 ? ne : (long)Nb_pad) % tile) continue;
+            c.tile = tile;
+            c.gather = gather;
+            auto run = [&]() {
+                if (which == 0) apply_global(p, DWF_OP_DDAGD, y, x, nullptr);
+                else apply_local(p, Ls_op, y, x, nullptr);
+            };
+            run();
+            DWF_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < reps; r++) run();
+            DWF_CUDA(cudaEventRecord(e1, st));
+            DWF_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            DWF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bestc = c;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c = bestc;
+    c.tuned = true;
 }
 
 int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part)
@@ -283,9 +403,12 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
     void *t1v = ws("g_t1_" + tag, fb);
     void *wv = ws("g_w_" + tag, fb);
     void *t3v = ws("g_t3_" + tag, fb);
-    const int tile = stage_tile(p);
+    const KCfg kc = kcfg(p, 0, Ls);
+    const int tile = kc.tile;
 
     StageArgs base{};
+    base.err = err_flag;
+    base.gather = kc.gather;
     base.tile_sys = tsys_e;
     base.mphi = m.mphi;
     base.nout = ne;
@@ -304,7 +427,7 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
         a.out = t1v;
         a.nbr = nbr_o;
         a.links = links(1, p);
-        a.F = matp(m, MK_S1F, p);
+        set_mats(a, m, p, MK_S1F, MK_N, TC_S1);
         launch_stage(p, MODE_F, true, a, st);
     };
     auto S2 = [&](const void *x, void *o, bool with_g) {
@@ -314,8 +437,8 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
         a.nbr = nbr_e;
         a.links = links(0, p);
         a.aux = x;
-        a.F = matp(m, MK_M5I, p);
-        a.G = with_g ? matp(m, MK_M5ID, p) : nullptr;
+        if (with_g) set_mats(a, m, p, MK_S2GF, MK_M5ID, TC_S2G);
+        else set_mats(a, m, p, MK_M5I, MK_N, TC_S2);
         launch_stage(p, MODE_S2, false, a, st);
     };
     auto S3 = [&](const void *w) {
@@ -324,7 +447,7 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
         a.out = t3v;
         a.nbr = nbr_o;
         a.links = links(1, p);
-        a.F = matp(m, MK_S3F, p);
+        set_mats(a, m, p, MK_S3F, MK_N, TC_S3);
         a.dagger = 1;
         launch_stage(p, MODE_F, false, a, st);
     };
@@ -335,8 +458,7 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
         a.nbr = nbr_e;
         a.links = links(0, p);
         a.aux = w;
-        a.F = matp(m, MK_S4F, p);
-        a.G = matp(m, MK_S4G, p);
+        set_mats(a, m, p, MK_S4F, MK_S4G, TC_S4);
         a.dagger = 1;
         a.dotv = dotv;
         a.dot_part = dot_part;
@@ -370,10 +492,13 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     void *t1v = ws("l_t1_" + tag, field_bytes(p, nO1, L));
     void *wv = ws("l_w_" + tag, field_bytes(p, nE2, L));
     void *t3v = ws("l_t3_" + tag, field_bytes(p, nO1, L));
-    const int tile = stage_tile(p);
+    const KCfg kc = kcfg(p, 1, L);
+    const int tile = kc.tile;
     const long nI = (long)nblk * Nb_pad;
 
     StageArgs a{};
+    a.err = err_flag;
+    a.gather = kc.gather;
     a.mphi = m.mphi;
     a.Ls = L;
     a.tile = tile;
@@ -387,10 +512,12 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     a.tile_sys = tsys_O1;
     a.seg_out = O1_pad;
     a.link_stride = O1_pad;
-    a.F = matp(m, MK_S1F, p);
+    set_mats(a, m, p, MK_S1F, MK_N, TC_S1);
     launch_stage(p, MODE_F, true, a, st);
     // S2: E2 <- O1, aux = interior x
     StageArgs b2{};
+    b2.err = err_flag;
+    b2.gather = kc.gather;
     b2.mphi = m.mphi;
     b2.Ls = L;
     b2.tile = tile;
@@ -407,11 +534,12 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b2.naux = nI;
     b2.aux_stride = Nb_pad;
     b2.aux_valid = Nb_pad;
-    b2.F = matp(m, MK_M5I, p);
-    b2.G = matp(m, MK_M5ID, p);
+    set_mats(b2, m, p, MK_S2GF, MK_M5ID, TC_S2G);
     launch_stage(p, MODE_S2, false, b2, st);
     // S3: O1 <- E2 (dagger)
     StageArgs b3{};
+    b3.err = err_flag;
+    b3.gather = kc.gather;
     b3.Ls = L;
     b3.tile = tile;
     b3.in = wv;
@@ -423,11 +551,13 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b3.tile_sys = tsys_O1;
     b3.seg_out = O1_pad;
     b3.link_stride = O1_pad;
-    b3.F = matp(m, MK_S3F, p);
+    set_mats(b3, m, p, MK_S3F, MK_N, TC_S3);
     b3.dagger = 1;
     launch_stage(p, MODE_F, false, b3, st);
     // S4: interior <- O1 (dagger), aux = w
     StageArgs b4{};
+    b4.err = err_flag;
+    b4.gather = kc.gather;
     b4.Ls = L;
     b4.tile = tile;
     b4.in = t3v;
@@ -443,9 +573,9 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b4.naux = nE2;
     b4.aux_stride = E2_pad;
     b4.aux_valid = Nb_pad;
-    b4.F = matp(m, MK_S4F, p);
-    b4.G = matp(m, MK_S4G, p);
+    set_mats(b4, m, p, MK_S4F, MK_S4G, TC_S4);
     b4.dagger = 1;
+    b4.mphi = m.mphi;
     b4.dotv = in;
     b4.dot_part = dot_part;
     launch_stage(p, MODE_S4, false, b4, st);

@@ -20,13 +20,28 @@ enum MatKind {
     MK_S3F,      // M5^-+ M_phi^+
     MK_S4F,      // M_phi^+
     MK_S4G,      // M5op^+
+    MK_S2GF,     // M5^-+ M5^-1
     MK_N
+};
+// Operand A of the tensor-core products: [G | -F] (or F alone) in FP16,
+// stored in the per-lane fragment order of mma m16n8k16:
+// [nsys][chi][k-step 2][lane 32] x 8 halves.
+enum TcKind {
+    TC_S1 = 0,   // F = M_phi M5^-1
+    TC_S2G,      // [M5^-+ | -M5^-+ M5^-1]
+    TC_S2,       // [1 | -M5^-1]
+    TC_S3,       // M5^-+ M_phi^+
+    TC_S4,       // [M5op^+ | -M_phi^+]
+    TC_M5I,      // M5^-1
+    TC_M5ID,     // M5^-+
+    TC_N
 };
 struct Mats {
     int Ls = 0;
     double *d64[MK_N] = {};
     float *d32[MK_N] = {};
-    double *mphi = nullptr;  // [nsys][3] = (b, c, mass)
+    void *tc[TC_N] = {};
+    double *mphi = nullptr;  // [nsys][5] = (b, c, mass, A, B)
 };
 
 struct SysInfo {
@@ -78,7 +93,22 @@ class Engine {
     int apply_local(Prec p, int Ls, void *out, const void *in, double *dot_part);
     void apply_5d(Prec p, int Ls, MatKind k, void *out, const void *in, long nsite);
 
-    static int stage_tile(Prec p) { return p == P64 ? 8 : 16; }
+    // Launch configuration of the hop stages of one operator (0 = global
+    // D^+D family, 1 = local operator) in one precision, chosen by autotune().
+    struct KCfg {
+        int tile = 8;
+        int gather = 0;
+        bool tuned = false;
+    };
+    KCfg cfg[2][4];
+    bool autotune_on = true;
+    // Times every fitting (tile, gather) candidate on this engine's lattice
+    // and keeps the fastest; `which` 0 global, 1 local at fifth extent Ls_op.
+    void autotune(Prec p, int which, int Ls_op, int reps = 5);
+    const KCfg &kcfg(Prec p, int which, int Ls_op);
+    // device flag raised by a bounded wait that gave up (reported as DWF_ETIMEOUT)
+    int *err_flag = nullptr;
+    bool check_err();  // reads and clears the flag (synchronizes the stream)
 
     // reduced Ls
     int Ls_hat = 0;

@@ -169,7 +169,7 @@ dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dw
     }
     const long long launches0 = launch_count();
     // workspace: the max CTA count over all kernels is n sites / 8-site tiles (x2 components)
-    const long max_cta = std::max<long>((long)E.nblk * E.E2_pad, n) / 8 + 16;
+    const long max_cta = std::max<long>((long)E.nblk * E.E2_pad, n) / 4 + 16;
     Ctx c{E, P, st, n, Ls, nsys, E.ws_d("part", 2 * max_cta)};
 
     void *x64 = E.ws("x64", field_bytes(P64, n, Ls));
@@ -357,6 +357,10 @@ dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dw
     }
     res.converged = ok;
     res.launches = launch_count() - launches0;
+    if (E.check_err()) {
+        err = "a bounded device wait gave up";
+        return DWF_ETIMEOUT;
+    }
     if (!ok) {
         err = "not converged within maxiter";
         return DWF_ENOCONV;
@@ -368,7 +372,7 @@ void precondition_fp64(Engine &E, double *z, const double *r, const dwf_solver_p
 {
     const long n = E.ne;
     const int Ls = E.Ls;
-    Ctx c{E, P, E.st, n, Ls, 1, E.ws_d("part", 2 * (std::max<long>((long)E.nblk * E.E2_pad, n) / 8 + 16))};
+    Ctx c{E, P, E.st, n, Ls, 1, E.ws_d("part", 2 * (std::max<long>((long)E.nblk * E.E2_pad, n) / 4 + 16))};
     void *r64 = E.ws("pc_r64", field_bytes(P64, n, Ls));
     void *r32 = E.ws("pc_r32", field_bytes(P32, n, Ls));
     void *z32 = E.ws("pc_z32", field_bytes(P32, n, Ls));
