@@ -440,13 +440,18 @@ __device__ __forceinline__ void su3_mul_half_smem(const R *U, const R *h, R *chi
         for (int q = 0; q < 6; q++) u[q] = U[r * 6 + q];
 #pragma unroll
         for (int sp = 0; sp < 2; sp++) {
-            R re = 0, im = 0;
+            const R *hp = h + sp * 6;
+            // complex dot product as a chain of fused multiply-adds
+            R re = u[0] * hp[0];
+            R im = u[0] * hp[1];
+            re = fma(-u[1], hp[1], re);
+            im = fma(u[1], hp[0], im);
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const R ur = u[2 * c], ui = u[2 * c + 1];
-                const R hr = h[(sp * 3 + c) * 2], hi = h[(sp * 3 + c) * 2 + 1];
-                re += ur * hr - ui * hi;
-                im += ur * hi + ui * hr;
+            for (int c = 1; c < 3; c++) {
+                re = fma(u[2 * c], hp[2 * c], re);
+                im = fma(u[2 * c], hp[2 * c + 1], im);
+                re = fma(-u[2 * c + 1], hp[2 * c + 1], re);
+                im = fma(u[2 * c + 1], hp[2 * c], im);
             }
             chi[(sp * 3 + r) * 2] = re;
             chi[(sp * 3 + r) * 2 + 1] = im;

@@ -1,789 +1,23 @@
-// Fused hop stage: one launch applies the Wilson hop D^w (or D^w^+) of
-// Sec. 2.2 on one checkerboard, followed by the fifth-dimension matrices that
-// follow it in Eq. (eq:detail) of Sec. 3.1.3, and optional axpy terms:
-//
-//   MODE_F : out = F . hop(in)
-//   MODE_S2: out = G . aux - (G F) . hop(in)       (G null: aux - F hop)
-//   MODE_S4: out = G . aux - F . hop(in)           (G null: aux - F hop), and a
-//            per-CTA partial of <dotv, out> (the <p, Ap> of CG)
-//   MODE_5D: out = F . in (no hop)
-// with, optionally, M_phi applied to every neighbour as it is loaded.
-//
-// The four stages of D^+D (Sec. 3.1.3, the five fused kernels) are composed as
-//   S1: t1 = [M_phi M5^-1] hop(M_phi x)          (MODE_F, M_phi on load)
-//   S2: w  = M5^-+ (x - M5^-1 hop(t1))           (MODE_S2)
-//   S3: t3 = [M5^-+ M_phi^+] hop^+(w)            (MODE_F)
-//   S4: D^+D x = M5op^+ w - M_phi^+ hop^+(t3)    (MODE_S4; M5op^+ w = D x)
-// Each F/G is an Ls x Ls real matrix per chirality.
-//
-// A CTA owns `tile` output 4D sites and all Ls slices (the Ls-slab of
-// Sec. 3.1.3 stays inside one CTA).  Data movement (FP32 / FP16 / BF16):
-// threads (j, k) issue bulk asynchronous copies (cp.async.bulk, the TMA
-// engine) of the whole Ls-column of neighbour k of site j, the link row of
-// site j, the FP16 scales and the aux / dot columns into shared memory,
-// completing on one mbarrier; the wait is bounded and raises an error flag
-// instead of hanging.  Thread (j, s) then computes the hop of 5D site (j, s)
-// from shared memory (the column also holds psi_{s+-1}, so M_phi costs no
-// extra loads).  The dense fifth-dimension products run
-//   - for FP16/BF16 storage on the tensor cores: [G | -F] (FP16, fixed per
-//     system) times [aux ; h] (FP16, scaled by the max-abs of the site as in
-//     Sec. 3.1.4) with FP32 accumulation, mma.sync m16n8k16 (Ls padded to 16);
-//   - for FP32/FP64 storage on the CUDA cores from shared memory.
-// FP64 (used only for reliable updates) loads neighbours directly.
-#include <type_traits>
-
-#include "device_common.cuh"
+// Stage launch dispatch by storage precision, and the launch-shape fit test
+// used by the autotuner (kernels: stage_impl.cuh, instantiated per precision
+// in stage_f64.cu, stage_f32.cu, stage_f16.cu, stage_bf16.cu).
+#include "stage_impl.cuh"
 
 namespace dwf {
 
-constexpr int kLinkStride = 20;  // reals per staged link (18 used, 16-byte aligned)
-
-// ------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    uint64_t state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    (void)state;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly),
-// records the failure and lets the CTA finish (results are then invalid and
-// the host reports DWF_ETIMEOUT).
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err)
-{
-    for (uint32_t it = 0; it < (1u << 22); it++)
-        if (mbar_try_wait(bar, phase)) return;
-    if (err) atomicExch(err, 1);
-}
-
-// ------------------------------------------------------------- helpers
-template <typename R>
-__device__ __forceinline__ void load_U(const R *sU, R *u);
-template <>
-__device__ __forceinline__ void load_U<float>(const float *sU, float *u)
-{
-    const float4 *p = reinterpret_cast<const float4 *>(sU);
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        float4 f = p[c];
-        u[4 * c] = f.x;
-        u[4 * c + 1] = f.y;
-        u[4 * c + 2] = f.z;
-        u[4 * c + 3] = f.w;
-    }
-    float2 f = reinterpret_cast<const float2 *>(sU)[8];
-    u[16] = f.x;
-    u[17] = f.y;
-}
-template <>
-__device__ __forceinline__ void load_U<double>(const double *sU, double *u)
-{
-    const double2 *p = reinterpret_cast<const double2 *>(sU);
-#pragma unroll
-    for (int c = 0; c < 9; c++) {
-        double2 f = p[c];
-        u[2 * c] = f.x;
-        u[2 * c + 1] = f.y;
-    }
-}
-
-// Decode the NC 16-byte chunks of one 5D spinor (stride `cs` chunks apart).
-template <class T>
-__device__ __forceinline__ void decode_chunks(const uint4 *p, int cs, typename T::R *v)
-{
-    if constexpr (T::P == P64) {
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-            const uint4 w = p[c * cs];
-            const double2 d = *reinterpret_cast<const double2 *>(&w);
-            v[2 * c] = d.x;
-            v[2 * c + 1] = d.y;
-        }
-    } else if constexpr (T::P == P32) {
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            const uint4 w = p[c * cs];
-            const float4 f = *reinterpret_cast<const float4 *>(&w);
-            v[4 * c] = f.x;
-            v[4 * c + 1] = f.y;
-            v[4 * c + 2] = f.z;
-            v[4 * c + 3] = f.w;
-        }
-    } else if constexpr (T::P == P16) {
-#pragma unroll
-        for (int c = 0; c < 3; c++) unpack8(p[c * cs], v + 8 * c, __half());
-    } else {
-#pragma unroll
-        for (int c = 0; c < 3; c++) unpack8(p[c * cs], v + 8 * c, __nv_bfloat16());
-    }
-}
-
-// acc[r] (+)= coef * sum_t M[chi(r)][s][t] X[t][r]; MT[t][s] holds (chi0, chi1) pairs
-template <typename R, bool kAdd>
-__device__ __forceinline__ void apply5(const R *MT, const R *X, int Ls, int s, R *acc, R coef)
-{
-    if (!kAdd) {
-#pragma unroll
-        for (int r = 0; r < 24; r++) acc[r] = 0;
-    }
-#pragma unroll 2
-    for (int t = 0; t < Ls; t++) {
-        const R f0 = coef * MT[(t * Ls + s) * 2];
-        const R f1 = coef * MT[(t * Ls + s) * 2 + 1];
-        const R *x = X + t * 24;
-        R xv[24];
-        if constexpr (sizeof(R) == 4) {
-            const float4 *q = reinterpret_cast<const float4 *>(x);
-#pragma unroll
-            for (int c = 0; c < 6; c++) {
-                float4 f = q[c];
-                xv[4 * c] = f.x;
-                xv[4 * c + 1] = f.y;
-                xv[4 * c + 2] = f.z;
-                xv[4 * c + 3] = f.w;
-            }
-        } else {
-            const double2 *q = reinterpret_cast<const double2 *>(x);
-#pragma unroll
-            for (int c = 0; c < 12; c++) {
-                double2 f = q[c];
-                xv[2 * c] = f.x;
-                xv[2 * c + 1] = f.y;
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < 12; r++) acc[r] += f0 * xv[r];
-#pragma unroll
-        for (int r = 12; r < 24; r++) acc[r] += f1 * xv[r];
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void store24(R *dst, const R *v)
-{
-    if constexpr (sizeof(R) == 4) {
-        float4 *q = reinterpret_cast<float4 *>(dst);
-#pragma unroll
-        for (int c = 0; c < 6; c++) q[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-    } else {
-#pragma unroll
-        for (int r = 0; r < 24; r++) dst[r] = v[r];
-    }
-}
-
-__device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
-{
-    __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-__device__ __forceinline__ void mma_16816(float *d, const uint4 &a, uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-
-// Shared-memory layout of a stage CTA (byte offsets), shared by host and device.
-struct StageSmem {
-    int bar, nbr, smax, lraw, U, mat, col, scl, aux, auxs, dot, dots, H, A, D, total;
-};
-__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
-__host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz, int rsz, bool tma,
-                                                bool tc, bool scale, bool has_aux, bool has_dot)
-{
-    StageSmem m;
-    const int colb = NC * Ls * 16;
-    int o = 0;
-    m.bar = o;
-    o = align16(o + 8);
-    m.nbr = o;
-    o = align16(o + TS * 8 * 4);
-    m.smax = o;
-    o = align16(o + TS * 4);
-    m.lraw = o;
-    o = align16(o + (tma ? TS * 96 * esz : 0));
-    m.U = o;
-    o = align16(o + TS * 8 * kLinkStride * rsz);
-    m.mat = o;
-    o = align16(o + (tc ? 0 : 4 * Ls * Ls * rsz));
-    m.aux = o;
-    o = align16(o + ((tma && has_aux) ? TS * colb : 0));
-    m.auxs = o;
-    o = align16(o + ((tma && has_aux && scale) ? TS * Ls * 4 : 0));
-    m.dot = o;
-    o = align16(o + ((tma && has_dot) ? TS * colb : 0));
-    m.dots = o;
-    o = align16(o + ((tma && has_dot && scale) ? TS * Ls * 4 : 0));
-    // neighbour columns; the hop result H and aux A alias them afterwards
-    const int hb = TS * Ls * 24 * rsz;
-    m.col = o;
-    m.scl = align16(o + (tma ? TS * 8 * colb : 0));
-    const int end_cols = align16(m.scl + ((tma && scale) ? TS * 8 * Ls * 4 : 0));
-    m.H = o;
-    m.A = align16(m.H + hb);
-    const int end_ha = align16(m.A + (has_aux ? hb : 0));
-    m.D = end_ha;  // tensor-core output when it cannot stay in registers
-    const int end_d = align16(m.D + hb);
-    m.total = end_cols > end_ha ? end_cols : end_ha;
-    if (tc) m.total = m.total > end_d ? m.total : end_d;
-    return m;
-}
-
-template <class T, int kMode, bool kMphi, bool kStage, bool kDag>
-__global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
-{
-    using R = typename T::R;
-    constexpr bool kTC = (T::P == P16 || T::P == PB16);
-    constexpr bool kScale = (T::P == P16);
-    constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
-    constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
-    constexpr int NC = T::NC;
-    using LE = typename LinkElem<T>::E;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int Ls = a.Ls, TS = a.tile;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int jl = tid / Ls;
-    const int s = tid - jl * Ls;
-    const bool active = jl < TS;
-    const long i0 = (long)blockIdx.x * TS;
-    const long i = i0 + (active ? jl : 0);
-    const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
-    const bool has_dot = (kMode == MODE_S4) && a.dot_part;
-    const bool scale_bulk = kScale && (Ls % 4 == 0);
-    const StageSmem L = stage_smem(TS, Ls, NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
-    int *sN = reinterpret_cast<int *>(smem_raw + L.nbr);
-    float *sMax = reinterpret_cast<float *>(smem_raw + L.smax);
-    R *sU = reinterpret_cast<R *>(smem_raw + L.U);
-    R *sX = reinterpret_cast<R *>(smem_raw + L.mat);
-    R *sH = reinterpret_cast<R *>(smem_raw + L.H);
-    R *sA = reinterpret_cast<R *>(smem_raw + L.A);
-    const int colb = NC * Ls * 16;
-    const uint4 *sCol = reinterpret_cast<const uint4 *>(smem_raw + L.col);
-    const float *sScl = reinterpret_cast<const float *>(smem_raw + L.scl);
-
-    const long seg = i / a.seg_out;
-    const long loc = i - seg * a.seg_out;
-
-    // fifth-dimension matrices for the CUDA-core path, transposed to [t][s][chi]
-    auto stage_mats = [&]() {
-        const R *Fg = reinterpret_cast<const R *>(a.F) + (size_t)sys * 2 * Ls * Ls;
-        const R *Gg = a.G ? reinterpret_cast<const R *>(a.G) + (size_t)sys * 2 * Ls * Ls : nullptr;
-        for (int e = tid; e < 2 * Ls * Ls; e += nthr) {
-            const int chi = e / (Ls * Ls), rem = e - chi * Ls * Ls;
-            const int ss = rem / Ls, t = rem - ss * Ls;
-            sX[(t * Ls + ss) * 2 + chi] = Fg[e];
-            if (Gg) sX[2 * Ls * Ls + (t * Ls + ss) * 2 + chi] = Gg[e];
-        }
-    };
-
-    // ---- 1. gather (bulk copies for FP32/16-bit, direct loads for FP64)
-    if constexpr (kTma) {
-        if (tid == 0) {
-            mbar_init(bar, TS * 8);
-            fence_mbar_init();
-        }
-        if (kTC && tid < TS) sMax[tid] = 0.f;
-        __syncthreads();
-        for (int e = tid; e < TS * 8; e += nthr) {
-            const int j = e >> 3, k = e & 7;
-            const long ii = i0 + j;
-            const long sg_ = ii / a.seg_out, lc = ii - sg_ * a.seg_out;
-            const int nb = __ldg(a.nbr + ii * 8 + k);
-            sN[e] = nb;
-            uint32_t bytes = 0;
-            const bool link = (k == 0);
-            const bool col = nb != -1;
-            const long idx = nb >= 0 ? (long)nb : (long)(-nb - 2);
-            // own aux / dot columns, issued by k = 1 / k = 2
-            const long ai = sg_ * a.aux_stride + lc;
-            const bool aux = kAux && k == 1 && (kMode == MODE_S4 || lc < a.aux_valid);
-            const bool dot = (kMode == MODE_S4) && k == 2 && a.dot_part;
-            const uint32_t sb = scale_bulk ? Ls * 4 : 0;
-            if (link) bytes += 96 * sizeof(LE);
-            if (col) bytes += colb + sb;
-            if (aux) bytes += colb + sb;
-            if (dot) bytes += colb + sb;
-            mbar_arrive_expect_tx(bar, bytes);
-            if (link) {
-                const long row = sg_ * a.link_stride + lc;
-                bulk_g2s(smem_raw + L.lraw + j * 96 * sizeof(LE),
-                         reinterpret_cast<const LE *>(a.links) + row * 96, 96 * sizeof(LE), bar);
-            }
-            if (col) {
-                bulk_g2s(smem_raw + L.col + e * colb, reinterpret_cast<const char *>(a.in) + idx * colb,
-                         colb, bar);
-                if (scale_bulk)
-                    bulk_g2s(smem_raw + L.scl + e * Ls * 4, scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls,
-                             sb, bar);
-            }
-            if (aux) {
-                bulk_g2s(smem_raw + L.aux + j * colb, reinterpret_cast<const char *>(a.aux) + ai * colb,
-                         colb, bar);
-                if (scale_bulk)
-                    bulk_g2s(smem_raw + L.auxs + j * Ls * 4, scale_ptr<TF16>(a.aux, a.naux, Ls) + ai * Ls,
-                             sb, bar);
-            }
-            if (dot) {
-                bulk_g2s(smem_raw + L.dot + j * colb, reinterpret_cast<const char *>(a.dotv) + ii * colb,
-                         colb, bar);
-                if (scale_bulk)
-                    bulk_g2s(smem_raw + L.dots + j * Ls * 4, scale_ptr<TF16>(a.dotv, a.nout, Ls) + ii * Ls,
-                             sb, bar);
-            }
-        }
-        if (!kTC) stage_mats();
-        mbar_wait_bounded(bar, 0, a.err);
-        // rebuild the third row of each staged link
-        for (int e = tid; e < TS * 8; e += nthr) {
-            const int j = e >> 3, k = e & 7;
-            R u[18];
-            const LE *lr = reinterpret_cast<const LE *>(smem_raw + L.lraw) + j * 96 + k * 12;
-#pragma unroll
-            for (int q = 0; q < 12; q++) {
-                if constexpr (sizeof(LE) == 2) u[q] = (R)__half2float(*reinterpret_cast<const __half *>(lr + q));
-                else u[q] = (R)lr[q];
-            }
-            reconstruct_row2<R>(u);
-            R *dst = sU + e * kLinkStride;
-#pragma unroll
-            for (int q = 0; q < 18; q++) dst[q] = u[q];
-        }
-        __syncthreads();
-    } else {
-        if (kMode != MODE_5D) {
-            for (int e = tid; e < TS * 8; e += nthr) {
-                const int j = e >> 3, k = e & 7;
-                const long ii = i0 + j;
-                const long sg_ = ii / a.seg_out;
-                const long row = sg_ * a.link_stride + (ii - sg_ * a.seg_out);
-                const int nb = __ldg(a.nbr + ii * 8 + k);
-                sN[e] = nb;
-                R u[18];
-                if (nb != -1) {
-                    load_link12<T>(a.links, row, k, u);
-                    reconstruct_row2<R>(u);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 18; q++) u[q] = 0;
-                }
-                R *dst = sU + e * kLinkStride;
-#pragma unroll
-                for (int q = 0; q < 18; q++) dst[q] = u[q];
-            }
-        }
-        if (kTC && tid < TS) sMax[tid] = 0.f;
-        if (!kTC) stage_mats();
-        __syncthreads();
-    }
-
-    // ---- 2. hop
-    R acc[24];
-#pragma unroll
-    for (int r = 0; r < 24; r++) acc[r] = 0;
-    if (kMode == MODE_5D) {
-        if (active) load_sp<T>(a.in, a.nin, i, s, Ls, acc);
-    } else if (active) {
-        R cb = 0, cc = 0, wm = 0;
-        if (kMphi) {
-            const double *mp = a.mphi + 5 * sys;
-            cb = (R)(-0.5 * mp[0]);
-            cc = (R)(-0.5 * mp[1]);
-            wm = (R)(-mp[2]);
-        }
-        const int sp = s + 1 < Ls ? s + 1 : 0;
-        const int sm1 = s > 0 ? s - 1 : Ls - 1;
-        // one direction k = 2 mu + d with compile-time mu and projector sign:
-        // forward (d = 0) 1 - gamma, backward 1 + gamma, flipped for D^w^+
-        auto dir = [&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr int mu = k >> 1;
-            constexpr int SG = ((k & 1) ? 1 : -1) * (kDag ? -1 : 1);
-            const int e = sN[jl * 8 + k];
-            if (e == -1) return;
-            const long idx = e >= 0 ? (long)e : (long)(-e - 2);
-            R psi[24];
-            R sc = 1;
-            if constexpr (kTma) {
-                const uint4 *cp = sCol + (size_t)(jl * 8 + k) * (colb / 16);
-                decode_chunks<T>(cp + s, Ls, psi);
-                if (kScale) {
-                    sc = scale_bulk ? sScl[(jl * 8 + k) * Ls + s]
-                                    : __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
-                }
-                if (kMphi) {
-                    // (M_phi psi)_s = -(b psi_s + c (P_- psi_{s+1} + P_+ psi_{s-1}))/2,
-                    // wrap terms times -mass; P_- = spins 0,1, P_+ = spins 2,3
-                    R q[24];
-                    R s1 = 1, s2 = 1;
-                    if (kScale) {
-                        s1 = scale_bulk ? sScl[(jl * 8 + k) * Ls + sp]
-                                        : __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + sp);
-                        s2 = scale_bulk ? sScl[(jl * 8 + k) * Ls + sm1]
-                                        : __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + sm1);
-                    }
-                    const R fp = (s + 1 < Ls ? cc : cc * wm) * s1;
-                    const R fm = (s > 0 ? cc : cc * wm) * s2;
-                    const R c0 = cb * sc;
-                    decode_chunks<T>(cp + sp, Ls, q);
-#pragma unroll
-                    for (int r = 0; r < 12; r++) psi[r] = c0 * psi[r] + fp * q[r];
-                    decode_chunks<T>(cp + sm1, Ls, q);
-#pragma unroll
-                    for (int r = 12; r < 24; r++) psi[r] = c0 * psi[r] + fm * q[r];
-                    sc = 1;
-                }
-            } else {
-                const uint4 *gp = reinterpret_cast<const uint4 *>(a.in) + (size_t)idx * NC * Ls;
-                uint4 raw[NC];
-#pragma unroll
-                for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + s);
-                if (kScale) sc = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
-                decode_chunks<T>(raw, 1, psi);
-                if (kMphi) {
-                    R q[24];
-                    R s1 = 1, s2 = 1;
-                    if (kScale) {
-                        s1 = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + sp);
-                        s2 = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + sm1);
-                    }
-                    const R fp = (s + 1 < Ls ? cc : cc * wm) * s1;
-                    const R fm = (s > 0 ? cc : cc * wm) * s2;
-                    const R c0 = cb * sc;
-#pragma unroll
-                    for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + sp);
-                    decode_chunks<T>(raw, 1, q);
-#pragma unroll
-                    for (int r = 0; r < 12; r++) psi[r] = c0 * psi[r] + fp * q[r];
-#pragma unroll
-                    for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + sm1);
-                    decode_chunks<T>(raw, 1, q);
-#pragma unroll
-                    for (int r = 12; r < 24; r++) psi[r] = c0 * psi[r] + fm * q[r];
-                    sc = 1;
-                }
-            }
-            R h[12], chi[12];
-            project_ct<mu, SG, R>(psi, e >= 0 ? sc : -sc, h);
-            su3_mul_half_smem<R>(sU + (jl * 8 + k) * kLinkStride, h, chi);
-            accumulate_ct<mu, SG, R>(chi, acc);
-        };
-        dir(std::integral_constant<int, 0>{});
-        dir(std::integral_constant<int, 1>{});
-        dir(std::integral_constant<int, 2>{});
-        dir(std::integral_constant<int, 3>{});
-        dir(std::integral_constant<int, 4>{});
-        dir(std::integral_constant<int, 5>{});
-        dir(std::integral_constant<int, 6>{});
-        dir(std::integral_constant<int, 7>{});
-    }
-
-    // own aux column
-    R av[24];
-#pragma unroll
-    for (int r = 0; r < 24; r++) av[r] = 0;
-    if (kAux) {
-        const bool aux_here = (kMode == MODE_S4) || loc < a.aux_valid;
-        if (active && aux_here) {
-            if constexpr (kTma) {
-                decode_chunks<T>(reinterpret_cast<const uint4 *>(smem_raw + L.aux) + jl * (colb / 16) + s, Ls, av);
-                if (kScale) {
-                    const float sa = scale_bulk ? reinterpret_cast<const float *>(smem_raw + L.auxs)[jl * Ls + s]
-                                                : __ldg(scale_ptr<TF16>(a.aux, a.naux, Ls) +
-                                                        (seg * a.aux_stride + loc) * Ls + s);
-#pragma unroll
-                    for (int r = 0; r < 24; r++) av[r] *= sa;
-                }
-            } else {
-                load_sp<T>(a.aux, a.naux, seg * a.aux_stride + loc, s, Ls, av);
-            }
-        }
-    }
-    if (kTma) {
-        // the neighbour columns (written by the async proxy) are reused below
-        fence_proxy_async_smem();
-        __syncthreads();
-    }
-
-    R out[24];
-    if constexpr (kMode == MODE_S4) {
-        // ---------------------------------------------------------------
-        // S4: out = M5op^+ aux - M_phi^+ h with both matrices bidiagonal per
-        // chirality: out = A aux + B P^T aux + (b h + c P^T h) / 2, where
-        // (P^T v)_s = v_{s-1} on spins 0,1 and v_{s+1} on spins 2,3 (wrap
-        // terms times -mass).  G null (the D^+ operator): out = aux + (b h + c P^T h)/2.
-        if (active) {
-            store24(sH + (jl * Ls + s) * 24, acc);
-            store24(sA + (jl * Ls + s) * 24, av);
-        }
-        __syncthreads();
-        if (active) {
-            const double *mp = a.mphi + 5 * sys;
-            const R hb = (R)(0.5 * mp[0]), hc = (R)(0.5 * mp[1]), mass = (R)mp[2];
-            const R cA = a.G ? (R)mp[3] : R(1), cB = a.G ? (R)mp[4] : R(0);
-            const int sm = s > 0 ? s - 1 : Ls - 1, sp = s + 1 < Ls ? s + 1 : 0;
-            const R flo = s > 0 ? R(1) : -mass, fhi = s + 1 < Ls ? R(1) : -mass;
-            const R *H0 = sH + (jl * Ls + s) * 24, *A0 = sA + (jl * Ls + s) * 24;
-            const R *Hm = sH + (jl * Ls + sm) * 24, *Am = sA + (jl * Ls + sm) * 24;
-            const R *Hp = sH + (jl * Ls + sp) * 24, *Ap = sA + (jl * Ls + sp) * 24;
-            const R bl = cB * flo, cl = hc * flo, bh = cB * fhi, ch = hc * fhi;
-#pragma unroll
-            for (int r = 0; r < 12; r++) out[r] = cA * A0[r] + bl * Am[r] + hb * H0[r] + cl * Hm[r];
-#pragma unroll
-            for (int r = 12; r < 24; r++) out[r] = cA * A0[r] + bh * Ap[r] + hb * H0[r] + ch * Hp[r];
-        }
-    } else if constexpr (kTC) {
-        // ---------------------------------------------------------------
-        // tensor-core path: B = [aux ; h] scaled per site, A = [G | -F] (FP16)
-        if (active) {
-            float m = 0.f;
-            store24(sH + (jl * Ls + s) * 24, acc);
-#pragma unroll
-            for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(acc[r]));
-            if (kAux) {
-                store24(sA + (jl * Ls + s) * 24, av);
-#pragma unroll
-                for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(av[r]));
-            }
-            atomicMax(reinterpret_cast<int *>(sMax + jl), __float_as_int(m));
-        }
-        __syncthreads();
-        const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-        const int g = lane >> 2, tg = lane & 3;
-        const int ntile = TS * 12 / 8;  // n-tiles per chirality
-        constexpr int nk = kAux ? 2 : 1;
-        const uint4 *Af = reinterpret_cast<const uint4 *>(a.F) + (size_t)sys * 2 * 2 * 32;
-        // results stay in registers (up to kMaxT tiles per warp) so that the
-        // output tile can overwrite sH; otherwise they go to a separate buffer
-        constexpr int kMaxT = 12;
-        const bool alias = (2 * ntile + nwarp - 1) / nwarp <= kMaxT;
-        R *sD = alias ? sH : reinterpret_cast<R *>(smem_raw + L.D);
-        float dreg[kMaxT][4];
-        auto tile_mma = [&](int qq, float *d) {
-            const int chi = qq / ntile, nt = qq - chi * ntile;
-            const int n = nt * 8 + g;  // this lane's B column
-            const int jb = n / 12, rb = chi * 12 + (n - jb * 12);
-            const float sig = sMax[jb];
-            const float inv = sig > 0.f ? 1.f / sig : 0.f;
-            d[0] = d[1] = d[2] = d[3] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < nk; kk++) {
-                // kk = 0: aux (if any) else h ; kk = 1: h
-                const R *X = (kAux && kk == 0) ? sA : sH;
-                const int t0 = 2 * tg, t1 = 2 * tg + 8;
-                const R *colp = X + (jb * Ls) * 24 + rb;
-                const float x0 = t0 < Ls ? colp[t0 * 24] * inv : 0.f;
-                const float x1 = t0 + 1 < Ls ? colp[(t0 + 1) * 24] * inv : 0.f;
-                const float x2 = t1 < Ls ? colp[t1 * 24] * inv : 0.f;
-                const float x3 = t1 + 1 < Ls ? colp[(t1 + 1) * 24] * inv : 0.f;
-                const uint4 af = __ldg(Af + ((chi * 2 + kk) * 32 + lane));
-                mma_16816(d, af, pack_h2(x0, x1), pack_h2(x2, x3));
-            }
-        };
-        auto tile_store = [&](int qq, const float *d) {
-            const int chi = qq / ntile, nt = qq - chi * ntile;
-            // D rows s = g, g + 8 ; columns nt*8 + 2 tg, +1 -> same site
-            const int nd = nt * 8 + 2 * tg;
-            const int jd = nd / 12, rd = chi * 12 + (nd - jd * 12);
-            const float sd = sMax[jd];
-            if (g < Ls)
-                *reinterpret_cast<float2 *>(sD + (jd * Ls + g) * 24 + rd) = make_float2(d[0] * sd, d[1] * sd);
-            if (g + 8 < Ls)
-                *reinterpret_cast<float2 *>(sD + (jd * Ls + g + 8) * 24 + rd) = make_float2(d[2] * sd, d[3] * sd);
-        };
-        if (alias) {
-#pragma unroll
-            for (int u = 0; u < kMaxT; u++) {
-                const int q = warp + u * nwarp;
-                if (q < 2 * ntile) tile_mma(q, dreg[u]);
-            }
-            __syncthreads();  // every warp has read sH / sA
-#pragma unroll
-            for (int u = 0; u < kMaxT; u++) {
-                const int q = warp + u * nwarp;
-                if (q < 2 * ntile) tile_store(q, dreg[u]);
-            }
-        } else {
-            for (int q = warp; q < 2 * ntile; q += nwarp) {
-                float d[4];
-                tile_mma(q, d);
-                tile_store(q, d);
-            }
-        }
-        __syncthreads();
-        if (active) {
-            const float4 *q4 = reinterpret_cast<const float4 *>(sD + (jl * Ls + s) * 24);
-#pragma unroll
-            for (int c = 0; c < 6; c++) {
-                float4 f = q4[c];
-                out[4 * c] = f.x;
-                out[4 * c + 1] = f.y;
-                out[4 * c + 2] = f.z;
-                out[4 * c + 3] = f.w;
-            }
-        }
-    } else {
-        // ---------------------------------------------------------------
-        // CUDA-core path (FP32 / FP64)
-        const R *sF = sX, *sG = sX + 2 * Ls * Ls;
-        if (active) {
-            store24(sH + (jl * Ls + s) * 24, acc);
-            if (kAux && a.G) store24(sA + (jl * Ls + s) * 24, av);
-        }
-        __syncthreads();
-        const R *Hsite = sH + jl * Ls * 24;
-        if (active) {
-            if (kMode == MODE_F || kMode == MODE_5D) {
-                apply5<R, false>(sF, Hsite, Ls, s, out, R(1));
-            } else {
-                // MODE_S2: out = G aux - F' h  (F' = G F; G null: aux - F h)
-                if (a.G) {
-                    apply5<R, false>(sG, sA + jl * Ls * 24, Ls, s, out, R(1));
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 24; r++) out[r] = av[r];
-                }
-                apply5<R, true>(sF, Hsite, Ls, s, out, R(-1));
-            }
-        }
-    }
-
-    if (active) store_sp<T>(a.out, a.nout, i, s, Ls, out);
-
-    if (kMode == MODE_S4 && a.dot_part) {
-        // partial <dotv, out> (real part), per thread in R, across threads in FP64
-        R dsum = 0;
-        if (active) {
-            R pv[24];
-            if constexpr (kTma) {
-                decode_chunks<T>(reinterpret_cast<const uint4 *>(smem_raw + L.dot) + jl * (colb / 16) + s, Ls, pv);
-                if (kScale) {
-                    const float sd = scale_bulk ? reinterpret_cast<const float *>(smem_raw + L.dots)[jl * Ls + s]
-                                                : __ldg(scale_ptr<TF16>(a.dotv, a.nout, Ls) + i * Ls + s);
-#pragma unroll
-                    for (int r = 0; r < 24; r++) pv[r] *= sd;
-                }
-            } else {
-                load_sp<T>(a.dotv, a.nout, i, s, Ls, pv);
-            }
-#pragma unroll
-            for (int r = 0; r < 24; r++) dsum += pv[r] * out[r];
-        }
-        double dd = (double)dsum;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
-        __shared__ double red[32];
-        if ((tid & 31) == 0) red[tid >> 5] = dd;
-        __syncthreads();
-        if (tid < 32) {
-            double v = tid < (nthr + 31) / 32 ? red[tid] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (tid == 0) a.dot_part[blockIdx.x] = v;
-        }
-    }
-}
-
-template <class T, int kMode, bool kMphi, bool kStage, bool kDag>
-static void launch_t(const StageArgs &a, cudaStream_t st)
-{
-    using R = typename T::R;
-    using LE = typename LinkElem<T>::E;
-    constexpr bool kTC = (T::P == P16 || T::P == PB16);
-    constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
-    constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
-    const int TS = a.tile, Ls = a.Ls;
-    const int nthr = (TS * Ls + 31) / 32 * 32;
-    const bool has_dot = (kMode == MODE_S4) && a.dot_part;
-    const bool scale_bulk = (T::P == P16) && (Ls % 4 == 0);
-    const StageSmem L = stage_smem(TS, Ls, T::NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot);
-    static bool attr_set = false;
-    if (!attr_set) {
-        DWF_CUDA(cudaFuncSetAttribute(stage_kernel<T, kMode, kMphi, kStage, kDag>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-        attr_set = true;
-    }
-    if (L.total > 220 * 1024) throw std::runtime_error("stage tile does not fit in shared memory");
-    const long nblk = a.nout / TS;
-    stage_kernel<T, kMode, kMphi, kStage, kDag><<<(unsigned)nblk, nthr, L.total, st>>>(a);
-    DWF_CUDA(cudaGetLastError());
-    count_launch();
-}
-
-template <class T, bool kStage>
-static void dispatch_mode(StageMode mode, bool mphi, const StageArgs &a, cudaStream_t st)
-{
-    // the combinations the operators use: S1 (F, M_phi), S2, S3 (F, dagger),
-    // S4 (dagger), and the fifth-dimension-only products
-    if (mode == MODE_F && mphi && !a.dagger) launch_t<T, MODE_F, true, kStage, false>(a, st);
-    else if (mode == MODE_F && !mphi && a.dagger) launch_t<T, MODE_F, false, kStage, true>(a, st);
-    else if (mode == MODE_F && !mphi && !a.dagger) launch_t<T, MODE_F, false, kStage, false>(a, st);
-    else if (mode == MODE_S2 && !mphi && !a.dagger) launch_t<T, MODE_S2, false, kStage, false>(a, st);
-    else if (mode == MODE_S4 && !mphi && a.dagger) launch_t<T, MODE_S4, false, kStage, true>(a, st);
-    else if (mode == MODE_5D) launch_t<T, MODE_5D, false, false, false>(a, st);
-    else throw std::runtime_error("unsupported stage combination");
-}
+extern template void launch_stage_prec<TF64>(StageMode, bool, const StageArgs &, cudaStream_t);
+extern template void launch_stage_prec<TF32>(StageMode, bool, const StageArgs &, cudaStream_t);
+extern template void launch_stage_prec<TF16>(StageMode, bool, const StageArgs &, cudaStream_t);
+extern template void launch_stage_prec<TBF16>(StageMode, bool, const StageArgs &, cudaStream_t);
 
 void launch_stage(Prec prec, StageMode mode, bool mphi_in, const StageArgs &a, cudaStream_t st)
 {
     if (a.nout == 0) return;
-    const bool bulk = a.gather == 1;
     switch (prec) {
-    case P64: dispatch_mode<TF64, false>(mode, mphi_in, a, st); break;
-    case P32:
-        if (bulk) dispatch_mode<TF32, true>(mode, mphi_in, a, st);
-        else dispatch_mode<TF32, false>(mode, mphi_in, a, st);
-        break;
-    case P16:
-        if (bulk) dispatch_mode<TF16, true>(mode, mphi_in, a, st);
-        else dispatch_mode<TF16, false>(mode, mphi_in, a, st);
-        break;
-    case PB16:
-        if (bulk) dispatch_mode<TBF16, true>(mode, mphi_in, a, st);
-        else dispatch_mode<TBF16, false>(mode, mphi_in, a, st);
-        break;
+    case P64: launch_stage_prec<TF64>(mode, mphi_in, a, st); break;
+    case P32: launch_stage_prec<TF32>(mode, mphi_in, a, st); break;
+    case P16: launch_stage_prec<TF16>(mode, mphi_in, a, st); break;
+    case PB16: launch_stage_prec<TBF16>(mode, mphi_in, a, st); break;
     }
 }
 
