@@ -180,6 +180,25 @@ void dwf_batch_destroy(dwf_batch *bt);
 dwf_status dwf_batch_mspcg(dwf_batch *bt, double *const *xs, const double *const *bs,
                            const dwf_solver_params *p, dwf_stats *per_system, dwf_stats *total);
 
+/* The global operators D, D^+ and D^+D (op as in dwf_apply) on packed fields,
+ * with no device memory allocated by the call.  The paper has no counterpart;
+ * this exists for callers that cannot allocate at this point (memory owned by
+ * an arena or pool, no allocator calls allowed while other work is in flight,
+ * hosts that forbid allocation after start-up).  The three intermediate fields
+ * live in one file-scope device array of 24 MiB that every GPU which loads
+ * this library holds until the process exits; lattices whose three fields in
+ * this precision need more (3 x dwf_packed_bytes rounded up to 256 bytes)
+ * are rejected with DWF_EINVAL.  Preconditions: one dwf_apply_packed call
+ * with the same precision on this handle (it builds the link copies, the
+ * fifth-dimension matrices and the launch configuration; this call never
+ * does).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, so calls whose
+ * work overlaps on the GPU (other streams, other handles, other threads)
+ * race; serialize them.  stream: 0 = the handle's stream. */
+dwf_status dwf_apply_packed_static(dwf_handle *h, void *out_dev, const void *in_dev, dwf_op op,
+                                   dwf_prec prec, void *stream);
+
 /* Last error message of a batch. */
 const char *dwf_batch_last_error(const dwf_batch *bt);
 

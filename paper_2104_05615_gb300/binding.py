@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
             "dwf_kernel_launch_count": (C.c_longlong, []),
             "dwf_get_geometry": (i, [vp, C.POINTER(dwf_geometry)]),
             "dwf_autotune": (i, [vp, i, i]),
+            "dwf_apply_packed_static": (i, [vp, vp, vp, i, i, vp]),
             "dwf_get_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
             "dwf_set_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
         }
@@ -172,6 +173,11 @@ def dwf_apply(h, out, inp, op, prec, stream=None):
 def dwf_apply_packed(h, out, inp, op, prec, stream=None):
     return check(lib().dwf_apply_packed(h, _ptr(out), _ptr(inp), int(op), int(prec),
                                         _stream(stream)), h)
+
+
+def dwf_apply_packed_static(h, out, inp, op, prec, stream=None):
+    return check(lib().dwf_apply_packed_static(h, _ptr(out), _ptr(inp), int(op), int(prec),
+                                               _stream(stream)), h)
 
 
 def dwf_pack(h, packed, canon, prec, stream=None):

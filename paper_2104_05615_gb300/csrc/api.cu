@@ -21,6 +21,9 @@ struct dwf_handle {
     std::vector<float> T;
 };
 
+dwf::Engine *dwf_handle_engine(dwf_handle *h) { return h->E.get(); }
+void dwf_handle_set_error(dwf_handle *h, const char *msg) { h->err = msg; }
+
 struct dwf_batch {
     std::vector<dwf_handle *> hs;
     std::unique_ptr<Engine> E;

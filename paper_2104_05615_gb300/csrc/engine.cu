@@ -395,14 +395,21 @@ void Engine::autotune(Prec p, int which, int Ls_op, int reps)
     c.tuned = true;
 }
 
-int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part)
+bool Engine::global_ready(Prec p) const
+{
+    const int cls = p == P64 ? 0 : p == P32 ? 1 : 2;
+    return lnk_[0][cls] && lnk_[1][cls] && mats_.count(Ls) && cfg[0][p].tuned;
+}
+
+int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part,
+                         void *const *scratch)
 {
     const Mats &m = mats(Ls);
     const size_t fb = field_bytes(p, ne, Ls);
     const std::string tag = std::to_string((int)p);
-    void *t1v = ws("g_t1_" + tag, fb);
-    void *wv = ws("g_w_" + tag, fb);
-    void *t3v = ws("g_t3_" + tag, fb);
+    void *t1v = scratch ? scratch[0] : ws("g_t1_" + tag, fb);
+    void *wv = scratch ? scratch[1] : ws("g_w_" + tag, fb);
+    void *t3v = scratch ? scratch[2] : ws("g_t3_" + tag, fb);
     const KCfg kc = kcfg(p, 0, Ls);
     const int tile = kc.tile;
 

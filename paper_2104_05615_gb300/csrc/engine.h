@@ -89,7 +89,13 @@ class Engine {
 
     // Operators on packed fields.  dot_part (optional): per-CTA partials of
     // <in, out> from the last stage; returns the CTA tile used.
-    int apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part);
+    // scratch (optional): three caller-provided fields of field_bytes(p, ne, Ls)
+    // bytes each, used instead of the engine's workspaces for t1, w, t3.
+    int apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part,
+                     void *const *scratch = nullptr);
+    // Has everything apply_global(p, ...) needs been created already (links,
+    // matrices, launch configuration), so that it would allocate nothing?
+    bool global_ready(Prec p) const;
     int apply_local(Prec p, int Ls, void *out, const void *in, double *dot_part);
     void apply_5d(Prec p, int Ls, MatKind k, void *out, const void *in, long nsite);
 
