@@ -14,6 +14,22 @@ Engine::~Engine()
 {
     for (void *p : owned_) cudaFree(p);
     for (auto &kv : ws_) cudaFree(kv.second.first);
+    if (pinned_) cudaFreeHost(pinned_);
+    if (solve_stream) cudaStreamDestroy(solve_stream);
+}
+
+double *Engine::pinned_d(size_t n)
+{
+    if (pinned_n_ < n) {
+        if (pinned_) {
+            DWF_CUDA(cudaStreamSynchronize(st));
+            cudaFreeHost(pinned_);
+            pinned_ = nullptr;
+        }
+        DWF_CUDA(cudaMallocHost(&pinned_, n * sizeof(double)));
+        pinned_n_ = n;
+    }
+    return pinned_;
 }
 
 template <class T>

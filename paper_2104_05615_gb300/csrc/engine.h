@@ -85,6 +85,9 @@ class Engine {
 
     // workspaces
     void *ws(const std::string &name, size_t bytes);
+    // page-locked host doubles (for asynchronous residual read-back)
+    double *pinned_d(size_t n);
+    cudaStream_t solve_stream = nullptr;  // private stream for graph-captured solves
     double *ws_d(const std::string &name, size_t n) { return (double *)ws(name, n * sizeof(double)); }
 
     // Operators on packed fields.  dot_part (optional): per-CTA partials of
@@ -126,6 +129,8 @@ class Engine {
     std::map<int, Mats> mats_;
     std::map<std::string, std::pair<void *, size_t>> ws_;
     std::vector<void *> owned_;
+    double *pinned_ = nullptr;
+    size_t pinned_n_ = 0;
     template <class T> T *upload(const std::vector<T> &h);
 };
 

@@ -22,6 +22,49 @@ namespace {
 
 constexpr int kBlasTile = 16;
 
+// A piece of the iteration replayed as one CUDA graph.  The first run() with
+// `use` captures the launches issued by f; later runs replay them.  Kernel
+// counts follow the replays.
+struct CapturedGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long nkern = 0;
+    CapturedGraph() = default;
+    CapturedGraph(const CapturedGraph &) = delete;
+    ~CapturedGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    template <class F>
+    void run(cudaStream_t st, bool use, F &&f)
+    {
+        if (!use) {
+            f();
+            return;
+        }
+        if (!exec) {
+            const long long c0 = launch_count();
+            DWF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            try {
+                f();
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(st, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            cudaGraph_t g = nullptr;
+            DWF_CUDA(cudaStreamEndCapture(st, &g));
+            const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            DWF_CUDA(e);
+            nkern = launch_count() - c0;
+            count_launch(-nkern);  // captured, not yet run
+        }
+        DWF_CUDA(cudaGraphLaunch(exec, st));
+        count_launch(nkern);
+    }
+};
+
 BlasArgs blas(long nsite, int Ls, const uint16_t *tile_seg, double *part)
 {
     BlasArgs a{};
@@ -147,8 +190,41 @@ void true_residual(Ctx &c, Prec po, void *x64, const void *b64, void *Ax64, void
 
 }  // namespace
 
+dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
+                      const dwf_solver_params &P, bool use_precond, SolveResult &res,
+                      std::string &err);
+
 dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dwf_solver_params &P,
                  bool use_precond, SolveResult &res, std::string &err)
+{
+    if (!P.use_graph) return solve_impl(E, xs, bs, P, use_precond, res, err);
+    // graphs cannot be captured on the legacy default stream: run the solve on
+    // the engine's own stream, ordered after and before the caller's stream
+    const cudaStream_t user = E.st;
+    if (!E.solve_stream) DWF_CUDA(cudaStreamCreateWithFlags(&E.solve_stream, cudaStreamNonBlocking));
+    cudaEvent_t ev;
+    DWF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    DWF_CUDA(cudaEventRecord(ev, user));
+    DWF_CUDA(cudaStreamWaitEvent(E.solve_stream, ev, 0));
+    E.st = E.solve_stream;
+    dwf_status s;
+    try {
+        s = solve_impl(E, xs, bs, P, use_precond, res, err);
+    } catch (...) {
+        E.st = user;
+        cudaEventDestroy(ev);
+        throw;
+    }
+    E.st = user;
+    DWF_CUDA(cudaEventRecord(ev, E.solve_stream));
+    DWF_CUDA(cudaStreamWaitEvent(user, ev, 0));
+    cudaEventDestroy(ev);
+    return s;
+}
+
+dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
+                      const dwf_solver_params &P, bool use_precond, SolveResult &res,
+                      std::string &err)
 {
     const cudaStream_t st = E.st;
     const long n = E.ne;
@@ -249,8 +325,11 @@ dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dw
     }
     const int maxiter = P.maxiter > 0 ? P.maxiter : 20000;
     const double delta2 = (P.delta > 0 ? P.delta : 0.1) * (P.delta > 0 ? P.delta : 0.1);
-    while (!converged && iters < maxiter) {
-        // alpha = <r,z> / <p, Ap>
+    // the two halves of an iteration; each becomes one CUDA graph after the
+    // first (uncaptured) iteration has tuned and allocated everything
+    double *h_rr_pin = E.pinned_d(nsys);
+    auto half1 = [&]() {
+        // alpha = <r,z> / <p, Ap> ; x += alpha p ; r -= alpha Ap ; |r|^2 to the host
         const int tile = E.apply_global(po, DWF_OP_DDAGD, Ap, p, c.part);
         {
             ScalarArgs s = scal(E.seg_sys, c.part, 1, tile);
@@ -259,21 +338,55 @@ dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dw
             s.s2 = pAp;
             launch_scalar(SC_ALPHA, s, st);
         }
-        {
-            BlasArgs a = blas(n, Ls, E.seg_sys.d_tile_seg, c.part);
-            a.v[0] = xacc; a.p[0] = po;
-            a.v[1] = p; a.p[1] = po;
-            a.v[2] = r; a.p[2] = po;
-            a.v[3] = Ap; a.p[3] = po;
-            a.scal[0] = al;
-            launch_blas(BLAS_CG_UPDATE, a, st);
+        BlasArgs a = blas(n, Ls, E.seg_sys.d_tile_seg, c.part);
+        a.v[0] = xacc; a.p[0] = po;
+        a.v[1] = p; a.p[1] = po;
+        a.v[2] = r; a.p[2] = po;
+        a.v[3] = Ap; a.p[3] = po;
+        a.scal[0] = al;
+        launch_blas(BLAS_CG_UPDATE, a, st);
+        ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
+        s.s0 = rr;
+        launch_scalar(SC_SUM, s, st);
+        DWF_CUDA(cudaMemcpyAsync(h_rr_pin, rr, nsys * 8, cudaMemcpyDeviceToHost, st));
+    };
+    int inner_in_half2 = 0;
+    auto half2 = [&]() {
+        // z = M^-1 r ; beta ; p = z + beta p
+        if (use_precond) {
+            precond_apply(c, po, r, z, inner_in_half2);
+            BlasArgs d = blas(n, Ls, nullptr, c.part);
+            d.v[0] = z; d.p[0] = po;
+            d.v[1] = r; d.p[1] = po;
+            d.v[2] = Ap; d.p[2] = po;
+            launch_blas(BLAS_DOT2, d, st);
+            ScalarArgs s = scal(E.seg_sys, c.part, 2, kBlasTile);
+            s.s0 = rz;
+            s.s1 = al;
+            s.s2 = be;
+            launch_scalar(SC_BETA_PR, s, st);
+        } else {
+            BlasArgs d = blas(n, Ls, nullptr, c.part);
+            d.v[0] = r; d.p[0] = po;
+            launch_blas(BLAS_NORM2, d, st);
             ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
-            s.s0 = rr;
-            launch_scalar(SC_SUM, s, st);
+            s.s0 = rz;
+            s.s1 = be;
+            launch_scalar(SC_BETA_FR, s, st);
         }
+        BlasArgs x = blas(n, Ls, E.seg_sys.d_tile_seg, nullptr);
+        x.v[0] = p; x.p[0] = po;
+        x.v[1] = z; x.p[1] = po;
+        x.scal[0] = be;
+        launch_blas(BLAS_XPAY, x, st);
+    };
+    CapturedGraph g1, g2;
+    while (!converged && iters < maxiter) {
+        const bool graph = P.use_graph && iters > 0;
+        g1.run(st, graph, half1);
         iters++;
-        DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
         DWF_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < nsys; k++) h_rr[k] = h_rr_pin[k];
         for (int k = 0; k < nsys; k++)
             if (!std::isfinite(h_rr[k])) {
                 err = "non-finite residual";
@@ -302,33 +415,8 @@ dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dw
                 break;
             }
         }
-        // z = M^-1 r ; beta ; p = z + beta p
-        if (use_precond) {
-            precond_apply(c, po, r, z, inner_total);
-            BlasArgs d = blas(n, Ls, nullptr, c.part);
-            d.v[0] = z; d.p[0] = po;
-            d.v[1] = r; d.p[1] = po;
-            d.v[2] = Ap; d.p[2] = po;
-            launch_blas(BLAS_DOT2, d, st);
-            ScalarArgs s = scal(E.seg_sys, c.part, 2, kBlasTile);
-            s.s0 = rz;
-            s.s1 = al;
-            s.s2 = be;
-            launch_scalar(SC_BETA_PR, s, st);
-        } else {
-            BlasArgs d = blas(n, Ls, nullptr, c.part);
-            d.v[0] = r; d.p[0] = po;
-            launch_blas(BLAS_NORM2, d, st);
-            ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
-            s.s0 = rz;
-            s.s1 = be;
-            launch_scalar(SC_BETA_FR, s, st);
-        }
-        BlasArgs x = blas(n, Ls, E.seg_sys.d_tile_seg, nullptr);
-        x.v[0] = p; x.p[0] = po;
-        x.v[1] = z; x.p[1] = po;
-        x.scal[0] = be;
-        launch_blas(BLAS_XPAY, x, st);
+        g2.run(st, graph, half2);
+        if (use_precond) inner_total += P.inner_iters;
     }
     // final solution and FP64 true residual
     if (po != P64) launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);

@@ -139,3 +139,17 @@ def test_noconvergence_reports_status(orc):
     assert not st.converged and st.outer_iters == 5
     # x holds the last iterate: a better residual than x = 0
     assert o.true_residual(x.cpu().numpy(), b) < 1.0
+
+
+@pytest.mark.gpu
+def test_graph_captured_solve_matches_direct_launches(orc):
+    """The outer iteration replayed as CUDA graphs gives the same iterates as
+    launching every kernel directly."""
+    lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
+    bd = torch.from_numpy(b).cuda()
+    lat.solve(bd, mspcg=True, tol=1e-10, inner_prec="f16", use_graph=0)  # tunes launch shapes
+    x1, s1 = lat.solve(bd, mspcg=True, tol=1e-10, inner_prec="f16", use_graph=1)
+    x0, s0 = lat.solve(bd, mspcg=True, tol=1e-10, inner_prec="f16", use_graph=0)
+    assert s1["outer_iters"] == s0["outer_iters"]
+    assert torch.equal(x1, x0)
+    assert s1["kernel_launches"] == s0["kernel_launches"]
