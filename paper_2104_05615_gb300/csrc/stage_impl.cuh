@@ -270,7 +270,7 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     // the tensor-core output needs its own buffer only when a warp has more
     // tiles than it keeps in registers (see the kernel's `alias`)
     const int nwarp = (TS * Ls + 31) / 32, ntile = TS * 12 / 8;
-    const bool alias = 2 * ((ntile + nwarp - 1) / nwarp) <= 12;
+    const bool alias = 2 * ((ntile + nwarp - 1) / nwarp) <= 8;
     if (tc && !alias) m.total = m.total > end_d ? m.total : end_d;
     return m;
 }
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
         const uint4 *Af = reinterpret_cast<const uint4 *>(a.F) + (size_t)sys * 2 * 2 * 32;
         // results stay in registers (up to kMaxT tiles per warp) so that the
         // output tile can overwrite sH; otherwise they go to a separate buffer
-        constexpr int kMaxT = 12;
+        constexpr int kMaxT = 8;
         const bool alias = 2 * ((ntile + nwarp - 1) / nwarp) <= kMaxT;
         R *sD = alias ? sH : reinterpret_cast<R *>(smem_raw + L.D);
         float dreg[kMaxT][4];
