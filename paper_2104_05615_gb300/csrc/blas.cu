@@ -116,6 +116,18 @@ __global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
     double p0 = 0, p1 = 0;
     const int seg = (active && a.tile_seg) ? a.tile_seg[i / kSegPad] : 0;
     const long n = a.nsite;
+    if (a.active) {
+        // converged systems of a batch are skipped (a CTA never straddles systems)
+        const long i0 = (long)blockIdx.x * a.tile;
+        const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
+        if (!a.active[sys]) {
+            if (a.part && threadIdx.x == 0) {
+                const int nc = op == BLAS_DOT2 ? 2 : 1;
+                for (int c = 0; c < nc; c++) a.part[(size_t)blockIdx.x * nc + c] = 0.0;
+            }
+            return;
+        }
+    }
     if (active) {
         R v0[24], v1[24], v2[24], v3[24];
         switch (op) {

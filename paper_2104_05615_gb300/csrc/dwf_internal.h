@@ -69,6 +69,7 @@ struct StageArgs {
     int aux_valid;       // aux present for local index < aux_valid
     int *err;            // device flag set when a bounded wait gives up (may be null)
     int gather;          // 0: direct neighbour loads; 1: bulk-copy staging in shared memory
+    const int *active;   // per system: 0 = converged, its CTAs exit at once (null: all active)
 };
 
 // Does a (tile, gather) choice fit the per-CTA limits for this precision and Ls?
@@ -120,6 +121,8 @@ struct BlasArgs {
     long nsite;
     int Ls;
     int tile;
+    const uint16_t *tile_sys;  // system of each kSegPad-site tile (with `active`)
+    const int *active;         // per system: 0 = converged, skip (null: all active)
 };
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st);
 

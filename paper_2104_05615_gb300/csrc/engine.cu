@@ -432,6 +432,7 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
     StageArgs base{};
     base.err = err_flag;
     base.gather = kc.gather;
+    base.active = active;
     base.tile_sys = tsys_e;
     base.mphi = m.mphi;
     base.nout = ne;
@@ -522,6 +523,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     StageArgs a{};
     a.err = err_flag;
     a.gather = kc.gather;
+    a.active = active;
     a.mphi = m.mphi;
     a.Ls = L;
     a.tile = tile;
@@ -541,6 +543,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     StageArgs b2{};
     b2.err = err_flag;
     b2.gather = kc.gather;
+    b2.active = active;
     b2.mphi = m.mphi;
     b2.Ls = L;
     b2.tile = tile;
@@ -563,6 +566,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     StageArgs b3{};
     b3.err = err_flag;
     b3.gather = kc.gather;
+    b3.active = active;
     b3.Ls = L;
     b3.tile = tile;
     b3.in = wv;
@@ -581,6 +585,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     StageArgs b4{};
     b4.err = err_flag;
     b4.gather = kc.gather;
+    b4.active = active;
     b4.Ls = L;
     b4.tile = tile;
     b4.in = t3v;

@@ -88,6 +88,8 @@ class Engine {
     // page-locked host doubles (for asynchronous residual read-back)
     double *pinned_d(size_t n);
     cudaStream_t solve_stream = nullptr;  // private stream for graph-captured solves
+    // per-system activity during a batched solve (device; null outside solves)
+    const int *active = nullptr;
     double *ws_d(const std::string &name, size_t n) { return (double *)ws(name, n * sizeof(double)); }
 
     // Operators on packed fields.  dot_part (optional): per-CTA partials of

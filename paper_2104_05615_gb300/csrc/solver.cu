@@ -65,9 +65,15 @@ struct CapturedGraph {
     }
 };
 
-BlasArgs blas(long nsite, int Ls, const uint16_t *tile_seg, double *part)
+// Arguments of a vector kernel; during a batched solve the engine's activity
+// mask makes the CTAs of converged systems exit at once.
+BlasArgs blas(const Engine &E, long nsite, int Ls, const uint16_t *tile_seg, double *part)
 {
     BlasArgs a{};
+    if (E.active) {
+        a.tile_sys = E.tsys_e;
+        a.active = E.active;
+    }
     a.nsite = nsite;
     a.Ls = Ls;
     a.tile = kBlasTile;
@@ -116,7 +122,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
 
     if (red) launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st);
     {
-        BlasArgs a = blas(n, L, tsb, c.part);
+        BlasArgs a = blas(E, n, L, tsb, c.part);
         a.v[0] = pin;
         a.p[0] = pi;
         a.v[1] = red ? rin : const_cast<void *>(r);
@@ -129,7 +135,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
         launch_scalar(SC_SUM, s, c.st);
     }
     {
-        BlasArgs a = blas(n, L, nullptr, nullptr);
+        BlasArgs a = blas(E, n, L, nullptr, nullptr);
         a.v[0] = zin;
         a.p[0] = P32;
         launch_blas(BLAS_AXPY_ZERO, a, c.st);
@@ -140,7 +146,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
         s.s0 = rr;
         s.s1 = al;
         launch_scalar(SC_ALPHA, s, c.st);
-        BlasArgs a = blas(n, L, tsb, c.part);
+        BlasArgs a = blas(E, n, L, tsb, c.part);
         a.v[0] = zin; a.p[0] = P32;
         a.v[1] = pin; a.p[1] = pi;
         a.v[2] = rin; a.p[2] = pi;
@@ -152,7 +158,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             t.s0 = rr;
             t.s1 = be;
             launch_scalar(SC_BETA_FR, t, c.st);
-            BlasArgs x = blas(n, L, tsb, nullptr);
+            BlasArgs x = blas(E, n, L, tsb, nullptr);
             x.v[0] = pin; x.p[0] = pi;
             x.v[1] = rin; x.p[1] = pi;
             x.scal[0] = be;
@@ -163,7 +169,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
     if (red) {
         launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st);
     } else if (P.inner_iters == 0) {
-        BlasArgs a = blas(n, E.Ls, nullptr, nullptr);
+        BlasArgs a = blas(E, n, E.Ls, nullptr, nullptr);
         a.v[0] = z;
         a.p[0] = po;
         launch_blas(BLAS_AXPY_ZERO, a, c.st);
@@ -177,7 +183,7 @@ void true_residual(Ctx &c, Prec po, void *x64, const void *b64, void *Ax64, void
                    double *rr)
 {
     c.E.apply_global(P64, DWF_OP_DDAGD, Ax64, x64, nullptr);
-    BlasArgs a = blas(c.n, c.Ls, nullptr, c.part);
+    BlasArgs a = blas(c.E, c.n, c.Ls, nullptr, c.part);
     a.v[0] = r64; a.p[0] = P64;
     a.v[1] = const_cast<void *>(b64); a.p[1] = P64;
     a.v[2] = Ax64; a.p[2] = P64;
@@ -273,7 +279,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
                     g.Vh, Ls, st);
     }
     {
-        BlasArgs a = blas(n, Ls, nullptr, c.part);
+        BlasArgs a = blas(E, n, Ls, nullptr, c.part);
         a.v[0] = b64;
         a.p[0] = P64;
         launch_blas(BLAS_NORM2, a, st);
@@ -285,7 +291,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     DWF_CUDA(cudaMemcpyAsync(h_bb.data(), bb, nsys * 8, cudaMemcpyDeviceToHost, st));
     true_residual(c, po, x64, b64, Ax64, r64, r, rr);
     if (po != P64) {
-        BlasArgs a = blas(n, Ls, nullptr, nullptr);
+        BlasArgs a = blas(E, n, Ls, nullptr, nullptr);
         a.v[0] = xacc;
         a.p[0] = po;
         launch_blas(BLAS_AXPY_ZERO, a, st);
@@ -311,11 +317,11 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     // p = z = M^-1 r ; rz = <r, z>
     if (!converged) {
         if (use_precond) precond_apply(c, po, r, z, inner_total);
-        BlasArgs a = blas(n, Ls, E.seg_sys.d_tile_seg, c.part);
+        BlasArgs a = blas(E, n, Ls, E.seg_sys.d_tile_seg, c.part);
         a.v[0] = p; a.p[0] = po;
         a.v[1] = z; a.p[1] = po;
         launch_blas(BLAS_COPY, a, st);  // partial |z|^2 unused
-        BlasArgs d = blas(n, Ls, nullptr, c.part);
+        BlasArgs d = blas(E, n, Ls, nullptr, c.part);
         d.v[0] = r; d.p[0] = po;
         d.v[1] = z; d.p[1] = po;
         launch_blas(BLAS_DOT, d, st);
@@ -338,7 +344,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             s.s2 = pAp;
             launch_scalar(SC_ALPHA, s, st);
         }
-        BlasArgs a = blas(n, Ls, E.seg_sys.d_tile_seg, c.part);
+        BlasArgs a = blas(E, n, Ls, E.seg_sys.d_tile_seg, c.part);
         a.v[0] = xacc; a.p[0] = po;
         a.v[1] = p; a.p[1] = po;
         a.v[2] = r; a.p[2] = po;
@@ -355,7 +361,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
         // z = M^-1 r ; beta ; p = z + beta p
         if (use_precond) {
             precond_apply(c, po, r, z, inner_in_half2);
-            BlasArgs d = blas(n, Ls, nullptr, c.part);
+            BlasArgs d = blas(E, n, Ls, nullptr, c.part);
             d.v[0] = z; d.p[0] = po;
             d.v[1] = r; d.p[1] = po;
             d.v[2] = Ap; d.p[2] = po;
@@ -366,7 +372,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             s.s2 = be;
             launch_scalar(SC_BETA_PR, s, st);
         } else {
-            BlasArgs d = blas(n, Ls, nullptr, c.part);
+            BlasArgs d = blas(E, n, Ls, nullptr, c.part);
             d.v[0] = r; d.p[0] = po;
             launch_blas(BLAS_NORM2, d, st);
             ScalarArgs s = scal(E.seg_sys, c.part, 1, kBlasTile);
@@ -374,12 +380,25 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             s.s1 = be;
             launch_scalar(SC_BETA_FR, s, st);
         }
-        BlasArgs x = blas(n, Ls, E.seg_sys.d_tile_seg, nullptr);
+        BlasArgs x = blas(E, n, Ls, E.seg_sys.d_tile_seg, nullptr);
         x.v[0] = p; x.p[0] = po;
         x.v[1] = z; x.p[1] = po;
         x.scal[0] = be;
         launch_blas(BLAS_XPAY, x, st);
     };
+    // per-system activity (batches only): converged systems' CTAs exit at once
+    std::vector<int> h_active(nsys, 1);
+    int *d_active = nullptr;
+    if (nsys > 1) {
+        d_active = (int *)E.ws("active", nsys * sizeof(int));
+        DWF_CUDA(cudaMemcpyAsync(d_active, h_active.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+        DWF_CUDA(cudaStreamSynchronize(st));
+    }
+    struct ActiveScope {
+        Engine &E;
+        ActiveScope(Engine &e, const int *a) : E(e) { E.active = a; }
+        ~ActiveScope() { E.active = nullptr; }
+    } active_scope(E, d_active);
     CapturedGraph g1, g2;
     while (!converged && iters < maxiter) {
         const bool graph = P.use_graph && iters > 0;
@@ -392,16 +411,22 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
                 err = "non-finite residual";
                 return DWF_ENOCONV;
             }
-        const bool conv_iter = all_below(h_rr);
-        bool do_ru = conv_iter && po != P64;
-        if (po != P64)
-            for (int k = 0; k < nsys; k++) {
+        // per-system decisions (a batch freezes systems once verified)
+        bool any_conv = false, changed = false;
+        bool do_ru = false;
+        for (int k = 0; k < nsys; k++) {
+            if (!h_active[k]) continue;
+            const bool ck = h_rr[k] <= tol2 * h_bb[k];
+            any_conv |= ck;
+            if (po == P64) {
+                if (ck) {
+                    h_active[k] = 0;
+                    changed = true;
+                }
+            } else {
                 h_max[k] = std::max(h_max[k], h_rr[k]);
-                if (h_rr[k] < delta2 * h_max[k]) do_ru = true;
+                if (ck || h_rr[k] < delta2 * h_max[k]) do_ru = true;
             }
-        if (po == P64 && conv_iter) {
-            converged = true;
-            break;
         }
         if (do_ru) {
             launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);
@@ -409,16 +434,32 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
             DWF_CUDA(cudaStreamSynchronize(st));
             ru++;
-            for (int k = 0; k < nsys; k++) h_max[k] = h_rr[k];
-            if (conv_iter && all_below(h_rr)) {
+            for (int k = 0; k < nsys; k++) {
+                h_max[k] = h_rr[k];
+                if (h_active[k] && any_conv && h_rr[k] <= tol2 * h_bb[k]) {
+                    h_active[k] = 0;
+                    changed = true;
+                }
+            }
+        }
+        if (changed) {
+            int left = 0;
+            for (int k = 0; k < nsys; k++) left += h_active[k];
+            if (left == 0) {
                 converged = true;
                 break;
+            }
+            if (d_active) {
+                DWF_CUDA(cudaMemcpyAsync(d_active, h_active.data(), nsys * sizeof(int),
+                                         cudaMemcpyHostToDevice, st));
+                DWF_CUDA(cudaStreamSynchronize(st));
             }
         }
         g2.run(st, graph, half2);
         if (use_precond) inner_total += P.inner_iters;
     }
-    // final solution and FP64 true residual
+    // final solution and FP64 true residual (every system)
+    E.active = nullptr;
     if (po != P64) launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);
     true_residual(c, po, x64, b64, Ax64, r64, r, rr);
     for (int k = 0; k < nsys; k++) {

@@ -295,6 +295,11 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
     const long i0 = (long)blockIdx.x * TS;
     const long i = i0 + (active ? jl : 0);
     const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
+    if (a.active && !a.active[sys]) {
+        // a converged system of a batch: nothing to do (whole CTA, one system)
+        if (kMode == MODE_S4 && a.dot_part && tid == 0) a.dot_part[blockIdx.x] = 0.0;
+        return;
+    }
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
     const bool scale_bulk = kScale && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
