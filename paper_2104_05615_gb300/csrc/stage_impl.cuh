@@ -126,6 +126,59 @@ __device__ __forceinline__ void load_U<double>(const double *sU, double *u)
     }
 }
 
+// One direction of the hop on an FP16 colour-spinor in packed half2
+// arithmetic: p[spin*3 + colour] = (re, im); U2 holds each link element as
+// (re, re), (-im, im).  chi = U h in half2, then accumulated in FP32 with the
+// neighbour's weight w (scale times boundary sign).
+__device__ __forceinline__ __half2 swap_h2(__half2 z) { return __lowhigh2highlow(z); }
+
+template <int MU, int SG>
+__device__ __forceinline__ void hop_dir_h2(const __half2 *p, const __half2 *U2, float w, float *acc)
+{
+    // i z = (-im, re) = swap(z) * (-1, 1)
+    const __half2 ipos = __floats2half2_rn(-1.f, 1.f);
+    const __half2 ineg = __floats2half2_rn(1.f, -1.f);
+    __half2 h[6];  // h[sp*3 + c]
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const __half2 p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+        if constexpr (MU == 0) {  // h0 = p0 + SG i p3, h1 = p1 + SG i p2
+            h[c] = __hfma2(swap_h2(p3), SG > 0 ? ipos : ineg, p0);
+            h[3 + c] = __hfma2(swap_h2(p2), SG > 0 ? ipos : ineg, p1);
+        } else if constexpr (MU == 1) {  // h0 = p0 + SG p3, h1 = p1 - SG p2
+            h[c] = SG > 0 ? __hadd2(p0, p3) : __hsub2(p0, p3);
+            h[3 + c] = SG > 0 ? __hsub2(p1, p2) : __hadd2(p1, p2);
+        } else if constexpr (MU == 2) {  // h0 = p0 + SG i p2, h1 = p1 - SG i p3
+            h[c] = __hfma2(swap_h2(p2), SG > 0 ? ipos : ineg, p0);
+            h[3 + c] = __hfma2(swap_h2(p3), SG > 0 ? ineg : ipos, p1);
+        } else {  // h0 = p0 + SG p2, h1 = p1 + SG p3
+            h[c] = SG > 0 ? __hadd2(p0, p2) : __hsub2(p0, p2);
+            h[3 + c] = SG > 0 ? __hadd2(p1, p3) : __hsub2(p1, p3);
+        }
+    }
+    __half2 hs[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) hs[q] = swap_h2(h[q]);
+    float chi[12];  // [sp][row][re, im]
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        const __half2 *Ur = U2 + r * 6;
+#pragma unroll
+        for (int sp = 0; sp < 2; sp++) {
+            __half2 t = __hmul2(Ur[0], h[sp * 3]);
+            t = __hfma2(Ur[1], hs[sp * 3], t);
+            t = __hfma2(Ur[2], h[sp * 3 + 1], t);
+            t = __hfma2(Ur[3], hs[sp * 3 + 1], t);
+            t = __hfma2(Ur[4], h[sp * 3 + 2], t);
+            t = __hfma2(Ur[5], hs[sp * 3 + 2], t);
+            const float2 f = __half22float2(t);
+            chi[(sp * 3 + r) * 2] = w * f.x;
+            chi[(sp * 3 + r) * 2 + 1] = w * f.y;
+        }
+    }
+    accumulate_ct<MU, SG, float>(chi, acc);
+}
+
 // Decode the NC 16-byte chunks of one 5D spinor (stride `cs` chunks apart).
 template <class T>
 __device__ __forceinline__ void decode_chunks(const uint4 *p, int cs, typename T::R *v)
@@ -284,6 +337,10 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
     constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
     constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
     constexpr int NC = T::NC;
+    // FP16 storage (values scaled to [-1, 1] per colour-spinor): projection and
+    // SU(3) products in packed half2 arithmetic, accumulation over the eight
+    // directions in FP32
+    constexpr bool kH2 = (T::P == P16) && !kMphi && !kTma && (kMode != MODE_5D);
     using LE = typename LinkElem<T>::E;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int Ls = LS > 0 ? LS : a.Ls;  // compile-time for the common fifth extents
@@ -420,9 +477,19 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
 #pragma unroll
                     for (int q = 0; q < 18; q++) u[q] = 0;
                 }
-                R *dst = sU + e * kLinkStride;
+                if constexpr (kH2) {
+                    // each element as two half2: (re, re) and (-im, im)
+                    __half2 *dst = reinterpret_cast<__half2 *>(sU + e * kLinkStride);
 #pragma unroll
-                for (int q = 0; q < 18; q++) dst[q] = u[q];
+                    for (int q = 0; q < 9; q++) {
+                        dst[2 * q] = __floats2half2_rn(u[2 * q], u[2 * q]);
+                        dst[2 * q + 1] = __floats2half2_rn(-u[2 * q + 1], u[2 * q + 1]);
+                    }
+                } else {
+                    R *dst = sU + e * kLinkStride;
+#pragma unroll
+                    for (int q = 0; q < 18; q++) dst[q] = u[q];
+                }
             }
         }
         if (kTC && tid < TS) sMax[tid] = 0.f;
@@ -486,6 +553,16 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
                     for (int r = 12; r < 24; r++) psi[r] = c0 * psi[r] + fm * q[r];
                     sc = 1;
                 }
+            } else if constexpr (kH2) {
+                const uint4 *gp = reinterpret_cast<const uint4 *>(a.in) + (size_t)idx * NC * Ls;
+                uint4 raw[NC];
+#pragma unroll
+                for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + s);
+                sc = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
+                hop_dir_h2<mu, SG>(reinterpret_cast<const __half2 *>(raw),
+                                   reinterpret_cast<const __half2 *>(sU + (jl * 8 + k) * kLinkStride),
+                                   e >= 0 ? sc : -sc, acc);
+                return;
             } else {
                 const uint4 *gp = reinterpret_cast<const uint4 *>(a.in) + (size_t)idx * NC * Ls;
                 uint4 raw[NC];
