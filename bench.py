@@ -342,7 +342,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves"],
                     help="ops: only apply the operators (for profilers)")
     ap.add_argument("--op-reps", type=int, default=3)
     ap.add_argument("--kcfg", default=None,
@@ -401,6 +401,27 @@ def main():
         tg = time_op(lat, B.DWF_OP_DDAGD, "f32", args.op_reps, flush)
         if rank == 0:
             print(json.dumps({"local_ms": tl * 1e3, "global_ms": tg * 1e3}))
+        return
+    if args.mode == "waves":
+        # the preconditioner alone (FP64 canonical in/out) for several wave sizes
+        from paper_2104_05615_gb300.lattice import PREC
+        z = torch.empty_like(bd)
+        for wave in (0, -1, 1, 2, 4, 8, 16):
+            p = solver_params(cfg, True)
+            p.precond_wave = wave
+            B.dwf_precondition(lat.h, z, bd, p)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(args.op_reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                B.dwf_precondition(lat.h, z, bd, p)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            if rank == 0:
+                print(json.dumps({"precond_wave": wave, "ms": statistics.mean(ts)}))
         return
     if args.mode == "sweep":
         # every fitting launch configuration of the inner local operator and of

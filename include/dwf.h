@@ -78,6 +78,9 @@ typedef struct {
     int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */
     int use_graph;         /* 1: capture each outer iteration in a CUDA graph */
     int check_every;       /* host convergence check period in outer iterations (>= 1) */
+    int precond_wave;      /* blocks whose k inner iterations run together (a "wave"):
+                              0 = all blocks (default), > 0 = that many, < 0 = as many as
+                              keep a wave's working set within half of L2 */
 } dwf_solver_params;
 
 typedef struct {

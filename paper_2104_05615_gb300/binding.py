@@ -22,7 +22,8 @@ DWF_OP_D, DWF_OP_DDAG, DWF_OP_DDAGD, DWF_OP_LOCAL_DDAGD, DWF_OP_M5INV, DWF_OP_M5
 class dwf_solver_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("inner_iters", C.c_int),
                 ("outer_prec", C.c_int), ("inner_prec", C.c_int), ("delta", C.c_double),
-                ("use_reduced_ls", C.c_int), ("use_graph", C.c_int), ("check_every", C.c_int)]
+                ("use_reduced_ls", C.c_int), ("use_graph", C.c_int), ("check_every", C.c_int),
+                ("precond_wave", C.c_int)]
 
 
 class dwf_geometry(C.Structure):

@@ -75,6 +75,7 @@ void dwf_default_params(dwf_solver_params *p)
     p->use_reduced_ls = 0;
     p->use_graph = 1;
     p->check_every = 1;
+    p->precond_wave = 0;
 }
 
 const char *dwf_status_string(dwf_status s)

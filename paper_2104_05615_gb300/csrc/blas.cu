@@ -77,7 +77,8 @@ __device__ __forceinline__ void store_any(Prec p, void *base, long nsite, long s
     }
 }
 
-__device__ __forceinline__ void block_reduce_store(double v0, double v1, int ncomp, double *part)
+__device__ __forceinline__ void block_reduce_store(double v0, double v1, int ncomp, double *part,
+                                                   long cta)
 {
     __shared__ double red[2][32];
 #pragma unroll
@@ -99,8 +100,8 @@ __device__ __forceinline__ void block_reduce_store(double v0, double v1, int nco
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
         if (tid == 0) {
-            part[(size_t)blockIdx.x * ncomp] = a;
-            if (ncomp > 1) part[(size_t)blockIdx.x * ncomp + 1] = b;
+            part[(size_t)cta * ncomp] = a;
+            if (ncomp > 1) part[(size_t)cta * ncomp + 1] = b;
         }
     }
 }
@@ -111,19 +112,20 @@ __global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
 {
     const int Ls = a.Ls;
     const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
-    const long i = (long)blockIdx.x * a.tile + jl;
-    const bool active = jl < a.tile && i < a.nsite;
+    const long i = a.site0 + (long)blockIdx.x * a.tile + jl;
+    const long cta = a.site0 / a.tile + blockIdx.x;  // absolute CTA index (partials)
+    const bool active = jl < a.tile && i < (a.site_end ? a.site_end : a.nsite);
     double p0 = 0, p1 = 0;
     const int seg = (active && a.tile_seg) ? a.tile_seg[i / kSegPad] : 0;
     const long n = a.nsite;
     if (a.active) {
         // converged systems of a batch are skipped (a CTA never straddles systems)
-        const long i0 = (long)blockIdx.x * a.tile;
+        const long i0 = a.site0 + (long)blockIdx.x * a.tile;
         const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
         if (!a.active[sys]) {
             if (a.part && threadIdx.x == 0) {
                 const int nc = op == BLAS_DOT2 ? 2 : 1;
-                for (int c = 0; c < nc; c++) a.part[(size_t)blockIdx.x * nc + c] = 0.0;
+                for (int c = 0; c < nc; c++) a.part[(size_t)cta * nc + c] = 0.0;
             }
             return;
         }
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
         } break;
         }
     }
-    if (a.part) block_reduce_store(p0, p1, op == BLAS_DOT2 ? 2 : 1, a.part);
+    if (a.part) block_reduce_store(p0, p1, op == BLAS_DOT2 ? 2 : 1, a.part, cta);
 }
 
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
@@ -221,7 +223,8 @@ void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
     for (int k = 0; k < 5; k++)
         if (a.v[k] && a.p[k] == P64) dbl = true;
     const int nthr = a.tile * a.Ls;
-    const unsigned nblk = (unsigned)((a.nsite + a.tile - 1) / a.tile);
+    const long end = a.site_end ? a.site_end : a.nsite;
+    const unsigned nblk = (unsigned)((end - a.site0 + a.tile - 1) / a.tile);
     if (dbl) blas_kernel<double><<<nblk, nthr, 0, st>>>(op, a);
     else blas_kernel<float><<<nblk, nthr, 0, st>>>(op, a);
     DWF_CUDA(cudaGetLastError());
@@ -388,7 +391,7 @@ void launch_unpack(Prec p, void *canon, const void *packed, const long *perm, lo
 // applies the recurrence.
 __global__ void scalar_kernel(ScalarOp op, ScalarArgs a)
 {
-    const int seg = blockIdx.x;
+    const int seg = a.seg0 + blockIdx.x;
     const long c0 = (long)a.tile_begin[seg] * kSegPad / a.sites_per_cta;
     const long c1 = (long)a.tile_begin[seg + 1] * kSegPad / a.sites_per_cta;
     double v0 = 0, v1 = 0;

@@ -70,6 +70,8 @@ struct StageArgs {
     int *err;            // device flag set when a bounded wait gives up (may be null)
     int gather;          // 0: direct neighbour loads; 1: bulk-copy staging in shared memory
     const int *active;   // per system: 0 = converged, its CTAs exit at once (null: all active)
+    long site0;          // first output site of this launch (a wave of blocks); indices stay absolute
+    long site_end;       // one past the last output site of this launch (0: nout)
 };
 
 // Does a (tile, gather) choice fit the per-CTA limits for this precision and Ls?
@@ -123,6 +125,8 @@ struct BlasArgs {
     int tile;
     const uint16_t *tile_sys;  // system of each kSegPad-site tile (with `active`)
     const int *active;         // per system: 0 = converged, skip (null: all active)
+    long site0;                // first site of this launch; sites [site0, site_end) are processed
+    long site_end;             // 0: nsite
 };
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st);
 
@@ -141,6 +145,7 @@ struct ScalarArgs {
     int cta_tiles;       // kSegPad-tiles per CTA of the partial producer (fractional not allowed)
     int sites_per_cta;   // sites per CTA of the producer
     double *s0, *s1, *s2, *s3;  // op-specific scalar arrays [nseg]
+    int seg0;            // first segment of this launch (nseg segments from seg0)
 };
 void launch_scalar(ScalarOp op, const ScalarArgs &a, cudaStream_t st);
 

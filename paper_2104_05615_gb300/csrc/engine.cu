@@ -156,6 +156,20 @@ void Engine::init(const std::vector<SysInfo> &sysv, int Ls_, double b_, double c
     err_flag = upload(std::vector<int>(1, 0));
 }
 
+int Engine::wave_blocks(Prec pi, int L)
+{
+    int dev = 0, l2 = 0;
+    DWF_CUDA(cudaGetDevice(&dev));
+    DWF_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    const size_t vec = 3 * field_bytes(pi, Nb_pad, L) + field_bytes(P32, Nb_pad, L);
+    const size_t halo = field_bytes(pi, 2L * O1_pad + E2_pad, L);
+    const size_t lnk = (size_t)(O1_pad + E2_pad) * 8 * 12 * 2;
+    const size_t tab = (size_t)(2L * O1_pad + E2_pad + Nb_pad) * 8 * 4;
+    const size_t per_block = vec + halo + lnk + tab;
+    const long w = (long)(0.5 * l2) / (long)per_block;
+    return (int)std::max<long>(1, std::min<long>(w, nblk));
+}
+
 bool Engine::check_err()
 {
     int h = 0;
@@ -509,8 +523,9 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
     return tile;
 }
 
-int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_part)
+int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_part, int b0, int b1)
 {
+    if (b1 < 0) b1 = nblk;
     const Mats &m = mats(L);
     const std::string tag = std::to_string((int)p) + "_" + std::to_string(L);
     void *t1v = ws("l_t1_" + tag, field_bytes(p, nO1, L));
@@ -537,6 +552,8 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     a.tile_sys = tsys_O1;
     a.seg_out = O1_pad;
     a.link_stride = O1_pad;
+    a.site0 = (long)b0 * O1_pad;
+    a.site_end = (long)b1 * O1_pad;
     set_mats(a, m, p, MK_S1F, MK_N, TC_S1);
     launch_stage(p, MODE_F, true, a, st);
     // S2: E2 <- O1, aux = interior x
@@ -556,6 +573,8 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b2.tile_sys = tsys_E2;
     b2.seg_out = E2_pad;
     b2.link_stride = E2_pad;
+    b2.site0 = (long)b0 * E2_pad;
+    b2.site_end = (long)b1 * E2_pad;
     b2.aux = in;
     b2.naux = nI;
     b2.aux_stride = Nb_pad;
@@ -578,6 +597,8 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b3.tile_sys = tsys_O1;
     b3.seg_out = O1_pad;
     b3.link_stride = O1_pad;
+    b3.site0 = (long)b0 * O1_pad;
+    b3.site_end = (long)b1 * O1_pad;
     set_mats(b3, m, p, MK_S3F, MK_N, TC_S3);
     b3.dagger = 1;
     launch_stage(p, MODE_F, false, b3, st);
@@ -597,6 +618,8 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b4.tile_sys = tsys_e;
     b4.seg_out = Nb_pad;
     b4.link_stride = E2_pad;
+    b4.site0 = (long)b0 * Nb_pad;
+    b4.site_end = (long)b1 * Nb_pad;
     b4.aux = wv;
     b4.naux = nE2;
     b4.aux_stride = E2_pad;

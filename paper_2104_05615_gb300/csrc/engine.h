@@ -85,6 +85,9 @@ class Engine {
 
     // workspaces
     void *ws(const std::string &name, size_t bytes);
+    // Blocks per preconditioner wave that keep the inner working set of a wave
+    // within half of L2.
+    int wave_blocks(Prec pi, int L);
     // page-locked host doubles (for asynchronous residual read-back)
     double *pinned_d(size_t n);
     cudaStream_t solve_stream = nullptr;  // private stream for graph-captured solves
@@ -101,7 +104,9 @@ class Engine {
     // Has everything apply_global(p, ...) needs been created already (links,
     // matrices, launch configuration), so that it would allocate nothing?
     bool global_ready(Prec p) const;
-    int apply_local(Prec p, int Ls, void *out, const void *in, double *dot_part);
+    // blocks [b0, b1) only (b1 < 0: all); indices stay absolute
+    int apply_local(Prec p, int Ls, void *out, const void *in, double *dot_part, int b0 = 0,
+                    int b1 = -1);
     void apply_5d(Prec p, int Ls, MatKind k, void *out, const void *in, long nsite);
 
     // Launch configuration of the hop stages of one operator (0 = global

@@ -104,7 +104,10 @@ struct Ctx {
     double *part;
 };
 
-// z = M^-1 r (outer precision po for r and z).
+// z = M^-1 r (outer precision po for r and z).  The blocks may be processed
+// in waves (all k inner iterations of one wave before the next); a wave whose
+// working set fits in L2 keeps the inner iterations off HBM.  The block-major
+// site order makes every wave a contiguous site range.
 void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
 {
     Engine &E = c.E;
@@ -121,51 +124,74 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
     const uint16_t *tsb = E.seg_blk.d_tile_seg;
 
     if (red) launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st);
-    {
-        BlasArgs a = blas(E, n, L, tsb, c.part);
-        a.v[0] = pin;
-        a.p[0] = pi;
-        a.v[1] = red ? rin : const_cast<void *>(r);
-        a.p[1] = red ? pi : po;
-        a.v[2] = red ? nullptr : rin;
-        a.p[2] = pi;
-        launch_blas(BLAS_COPY, a, c.st);
-        ScalarArgs s = scal(E.seg_blk, c.part, 1, kBlasTile);
-        s.s0 = rr;
-        launch_scalar(SC_SUM, s, c.st);
-    }
-    {
-        BlasArgs a = blas(E, n, L, nullptr, nullptr);
-        a.v[0] = zin;
-        a.p[0] = P32;
-        launch_blas(BLAS_AXPY_ZERO, a, c.st);
-    }
-    for (int it = 0; it < P.inner_iters; it++) {
-        const int tile = E.apply_local(pi, L, Apin, pin, c.part);
-        ScalarArgs s = scal(E.seg_blk, c.part, 1, tile);
-        s.s0 = rr;
-        s.s1 = al;
-        launch_scalar(SC_ALPHA, s, c.st);
-        BlasArgs a = blas(E, n, L, tsb, c.part);
-        a.v[0] = zin; a.p[0] = P32;
-        a.v[1] = pin; a.p[1] = pi;
-        a.v[2] = rin; a.p[2] = pi;
-        a.v[3] = Apin; a.p[3] = pi;
-        a.scal[0] = al;
-        launch_blas(BLAS_CG_UPDATE, a, c.st);
-        if (it + 1 < P.inner_iters) {
+    // default: every block in one wave (measured fastest on GB300: smaller,
+    // L2-resident waves leave the latency-bound stages short of parallelism)
+    const int wave = P.precond_wave > 0 ? std::min(P.precond_wave, E.nblk)
+                     : P.precond_wave < 0 ? E.wave_blocks(pi, L) : E.nblk;
+    for (int b0 = 0; b0 < E.nblk; b0 += wave) {
+        const int b1 = std::min(E.nblk, b0 + wave);
+        const long s0 = (long)b0 * E.Nb_pad, s1 = (long)b1 * E.Nb_pad;
+        auto range = [&](BlasArgs &a) {
+            a.site0 = s0;
+            a.site_end = s1;
+        };
+        auto segs = [&](ScalarArgs &t) {
+            t.seg0 = b0;
+            t.nseg = b1 - b0;
+        };
+        {
+            BlasArgs a = blas(E, n, L, tsb, c.part);
+            range(a);
+            a.v[0] = pin;
+            a.p[0] = pi;
+            a.v[1] = red ? rin : const_cast<void *>(r);
+            a.p[1] = red ? pi : po;
+            a.v[2] = red ? nullptr : rin;
+            a.p[2] = pi;
+            launch_blas(BLAS_COPY, a, c.st);
             ScalarArgs t = scal(E.seg_blk, c.part, 1, kBlasTile);
+            segs(t);
             t.s0 = rr;
-            t.s1 = be;
-            launch_scalar(SC_BETA_FR, t, c.st);
-            BlasArgs x = blas(E, n, L, tsb, nullptr);
-            x.v[0] = pin; x.p[0] = pi;
-            x.v[1] = rin; x.p[1] = pi;
-            x.scal[0] = be;
-            launch_blas(BLAS_XPAY, x, c.st);
+            launch_scalar(SC_SUM, t, c.st);
         }
-        inner_count++;
+        {
+            BlasArgs a = blas(E, n, L, nullptr, nullptr);
+            range(a);
+            a.v[0] = zin;
+            a.p[0] = P32;
+            launch_blas(BLAS_AXPY_ZERO, a, c.st);
+        }
+        for (int it = 0; it < P.inner_iters; it++) {
+            const int tile = E.apply_local(pi, L, Apin, pin, c.part, b0, b1);
+            ScalarArgs t = scal(E.seg_blk, c.part, 1, tile);
+            segs(t);
+            t.s0 = rr;
+            t.s1 = al;
+            launch_scalar(SC_ALPHA, t, c.st);
+            BlasArgs a = blas(E, n, L, tsb, c.part);
+            range(a);
+            a.v[0] = zin; a.p[0] = P32;
+            a.v[1] = pin; a.p[1] = pi;
+            a.v[2] = rin; a.p[2] = pi;
+            a.v[3] = Apin; a.p[3] = pi;
+            a.scal[0] = al;
+            launch_blas(BLAS_CG_UPDATE, a, c.st);
+            if (it + 1 < P.inner_iters) {
+                ScalarArgs u = scal(E.seg_blk, c.part, 1, kBlasTile);
+                segs(u);
+                u.s0 = rr;
+                u.s1 = be;
+                launch_scalar(SC_BETA_FR, u, c.st);
+                BlasArgs x = blas(E, n, L, tsb, nullptr);
+                range(x);
+                x.v[0] = pin; x.p[0] = pi;
+                x.v[1] = rin; x.p[1] = pi;
+                x.scal[0] = be;
+                launch_blas(BLAS_XPAY, x, c.st);
+            }
+        }
     }
+    inner_count += P.inner_iters;
     if (red) {
         launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st);
     } else if (P.inner_iters == 0) {
