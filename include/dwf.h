@@ -78,6 +78,8 @@ typedef struct {
     int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */
     int use_graph;         /* 1: capture each outer iteration in a CUDA graph */
     int check_every;       /* host convergence check period in outer iterations (>= 1) */
+    int time_kernels;      /* 1: time every operator application with CUDA events on the
+                              solve's stream (reported in dwf_stats) */
     int precond_wave;      /* blocks whose k inner iterations run together (a "wave"):
                               0 = all blocks (default), > 0 = that many, < 0 = as many as
                               keep a wave's working set within half of L2 */
@@ -91,6 +93,11 @@ typedef struct {
     double true_residual;     /* FP64 ||b - D^+D x|| / ||b|| at exit (per system for batches) */
     double time_total_ms;     /* device time of the solve (events on the handle's stream) */
     long long kernel_launches;/* kernels this call launched (graph nodes counted per replay) */
+    double local_op_ms;       /* with time_kernels: summed device time of the local-operator
+                                 applications of the preconditioner (4 hop stages each) */
+    long long local_op_count;
+    double outer_op_ms;       /* with time_kernels: summed device time of the outer D^+D */
+    long long outer_op_count;
 } dwf_stats;
 
 /* Default parameters: tol 1e-10, maxiter 20000, k 6, FP32 outer, FP16 inner,

@@ -23,7 +23,7 @@ class dwf_solver_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("inner_iters", C.c_int),
                 ("outer_prec", C.c_int), ("inner_prec", C.c_int), ("delta", C.c_double),
                 ("use_reduced_ls", C.c_int), ("use_graph", C.c_int), ("check_every", C.c_int),
-                ("precond_wave", C.c_int)]
+                ("time_kernels", C.c_int), ("precond_wave", C.c_int)]
 
 
 class dwf_geometry(C.Structure):
@@ -43,7 +43,9 @@ class dwf_stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int),
                 ("reliable_updates", C.c_int), ("converged", C.c_int),
                 ("true_residual", C.c_double), ("time_total_ms", C.c_double),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("local_op_ms", C.c_double),
+                ("local_op_count", C.c_longlong), ("outer_op_ms", C.c_double),
+                ("outer_op_count", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -75,6 +75,7 @@ void dwf_default_params(dwf_solver_params *p)
     p->use_reduced_ls = 0;
     p->use_graph = 1;
     p->check_every = 1;
+    p->time_kernels = 0;
     p->precond_wave = 0;
 }
 
@@ -251,6 +252,10 @@ static dwf_status run_solve(dwf_handle *h, double *x, const double *b, const dwf
             stats->true_residual = r.true_res.empty() ? -1.0 : r.true_res[0];
             stats->time_total_ms = r.ms;
             stats->kernel_launches = r.launches;
+            stats->local_op_ms = r.local_ms;
+            stats->local_op_count = r.local_n;
+            stats->outer_op_ms = r.outer_ms;
+            stats->outer_op_count = r.outer_n;
         }
         return s;
     });
@@ -379,6 +384,10 @@ dwf_status dwf_batch_mspcg(dwf_batch *bt, double *const *xs, const double *const
             total->true_residual = mx;
             total->time_total_ms = r.ms;
             total->kernel_launches = r.launches;
+            total->local_op_ms = r.local_ms;
+            total->local_op_count = r.local_n;
+            total->outer_op_ms = r.outer_ms;
+            total->outer_op_count = r.outer_n;
         }
         return s;
     });

@@ -213,6 +213,34 @@ __global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
         } break;
         }
     }
+    if (a.mphi_out) {
+        // u = M_phi v for the vector just written: the CTA holds whole Ls
+        // columns, so psi_{s+-1} of the same site come from shared memory.
+        // (M_phi v)_s = -(b v_s + c (P_- v_{s+1} + P_+ v_{s-1}))/2, wraps times -mass.
+        extern __shared__ __align__(16) unsigned char blas_smem[];
+        R *sv = reinterpret_cast<R *>(blas_smem);
+        R v[24];
+        if (active) load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v);
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < 24; r++) sv[(jl * Ls + s) * 24 + r] = v[r];
+        }
+        __syncthreads();
+        if (active) {
+            const int sys = a.tile_sys ? a.tile_sys[i / kSegPad] : 0;
+            const double *mp = a.mphi + 5 * sys;
+            const R cb = (R)(-0.5 * mp[0]), cc = (R)(-0.5 * mp[1]), wm = (R)(-mp[2]);
+            const int sp = s + 1 < Ls ? s + 1 : 0, sm = s > 0 ? s - 1 : Ls - 1;
+            const R fp = s + 1 < Ls ? cc : cc * wm, fm = s > 0 ? cc : cc * wm;
+            const R *vp = sv + (jl * Ls + sp) * 24, *vm = sv + (jl * Ls + sm) * 24;
+            R u[24];
+#pragma unroll
+            for (int r = 0; r < 12; r++) u[r] = cb * v[r] + fp * vp[r];
+#pragma unroll
+            for (int r = 12; r < 24; r++) u[r] = cb * v[r] + fm * vm[r];
+            store_any<R>(a.mphi_prec, a.mphi_out, n, i, s, Ls, u);
+        }
+    }
     if (a.part) block_reduce_store(p0, p1, op == BLAS_DOT2 ? 2 : 1, a.part, cta);
 }
 
@@ -225,8 +253,9 @@ void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
     const int nthr = a.tile * a.Ls;
     const long end = a.site_end ? a.site_end : a.nsite;
     const unsigned nblk = (unsigned)((end - a.site0 + a.tile - 1) / a.tile);
-    if (dbl) blas_kernel<double><<<nblk, nthr, 0, st>>>(op, a);
-    else blas_kernel<float><<<nblk, nthr, 0, st>>>(op, a);
+    const size_t sm = a.mphi_out ? (size_t)nthr * 24 * (dbl ? 8 : 4) : 0;
+    if (dbl) blas_kernel<double><<<nblk, nthr, sm, st>>>(op, a);
+    else blas_kernel<float><<<nblk, nthr, sm, st>>>(op, a);
     DWF_CUDA(cudaGetLastError());
     count_launch();
 }

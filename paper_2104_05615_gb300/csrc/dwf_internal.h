@@ -127,6 +127,11 @@ struct BlasArgs {
     const int *active;         // per system: 0 = converged, skip (null: all active)
     long site0;                // first site of this launch; sites [site0, site_end) are processed
     long site_end;             // 0: nsite
+    // BLAS_COPY / BLAS_XPAY: also write u = M_phi v (v the vector written to v[0]),
+    // M_phi = -(b + c P)/2 per system (mphi = [nsys][5] = b, c, mass, ...)
+    void *mphi_out;
+    Prec mphi_prec;
+    const double *mphi;
 };
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st);
 

@@ -10,8 +10,67 @@
 
 namespace dwf {
 
+// Under stream capture the record must be an external event node, so that
+// every replay of the graph re-records the event; outside capture the flag is
+// refused and a plain record is taken.
+static void record_timing_event(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DWF_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+        DWF_CUDA(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+    else
+        DWF_CUDA(cudaEventRecord(ev, st));
+}
+
+void Engine::timed_begin(int slot)
+{
+    if (!time_kernels) return;
+    if ((int)tev_used.size() <= slot) {
+        const int old = (int)tev_used.size();
+        tev.resize(2 * (slot + 1));
+        tev_used.resize(slot + 1, 0);
+        for (int k = 2 * old; k < 2 * (slot + 1); k++) DWF_CUDA(cudaEventCreate(&tev[k]));
+    }
+    record_timing_event(tev[2 * slot], st);
+}
+
+void Engine::timed_end(int slot)
+{
+    if (!time_kernels) return;
+    record_timing_event(tev[2 * slot + 1], st);
+}
+
+void Engine::timed_mark(int first, int count)
+{
+    if (!time_kernels) return;
+    for (int k = first; k < first + count && k < (int)tev_used.size(); k++) tev_used[k] = 1;
+}
+
+void Engine::timed_collect(double &outer_ms, long long &outer_n, double &local_ms, long long &local_n)
+{
+    for (size_t k = 0; k < tev_used.size(); k++) {
+        if (!tev_used[k]) continue;
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, tev[2 * k], tev[2 * k + 1]) != cudaSuccess) {
+            cudaGetLastError();  // timing unavailable for this pair: skip it
+            tev_used[k] = 0;
+            continue;
+        }
+        if (k == 0) {
+            outer_ms += ms;
+            outer_n++;
+        } else {
+            local_ms += ms;
+            local_n++;
+        }
+        tev_used[k] = 0;
+    }
+}
+
 Engine::~Engine()
 {
+    for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
     for (void *p : owned_) cudaFree(p);
     for (auto &kv : ws_) cudaFree(kv.second.first);
     if (pinned_) cudaFreeHost(pinned_);
@@ -432,7 +491,7 @@ bool Engine::global_ready(Prec p) const
 }
 
 int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part,
-                         void *const *scratch)
+                         void *const *scratch, const void *in_mphi)
 {
     const Mats &m = mats(Ls);
     const size_t fb = field_bytes(p, ne, Ls);
@@ -461,12 +520,12 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
 
     auto S1 = [&](const void *x) {
         StageArgs a = base;
-        a.in = x;
+        a.in = in_mphi ? in_mphi : x;
         a.out = t1v;
         a.nbr = nbr_o;
         a.links = links(1, p);
         set_mats(a, m, p, MK_S1F, MK_N, TC_S1);
-        launch_stage(p, MODE_F, true, a, st);
+        launch_stage(p, MODE_F, in_mphi == nullptr, a, st);
     };
     auto S2 = [&](const void *x, void *o, bool with_g) {
         StageArgs a = base;
@@ -523,7 +582,8 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
     return tile;
 }
 
-int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_part, int b0, int b1)
+int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_part, int b0, int b1,
+                        const void *in_mphi)
 {
     if (b1 < 0) b1 = nblk;
     const Mats &m = mats(L);
@@ -542,8 +602,8 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     a.mphi = m.mphi;
     a.Ls = L;
     a.tile = tile;
-    // S1: O1 <- interior
-    a.in = in;
+    // S1: O1 <- interior (M_phi applied on load unless the producer gave in_mphi)
+    a.in = in_mphi ? in_mphi : in;
     a.nin = nI;
     a.out = t1v;
     a.nout = nO1;
@@ -555,7 +615,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     a.site0 = (long)b0 * O1_pad;
     a.site_end = (long)b1 * O1_pad;
     set_mats(a, m, p, MK_S1F, MK_N, TC_S1);
-    launch_stage(p, MODE_F, true, a, st);
+    launch_stage(p, MODE_F, in_mphi == nullptr, a, st);
     // S2: E2 <- O1, aux = interior x
     StageArgs b2{};
     b2.err = err_flag;

@@ -91,6 +91,18 @@ class Engine {
     // page-locked host doubles (for asynchronous residual read-back)
     double *pinned_d(size_t n);
     cudaStream_t solve_stream = nullptr;  // private stream for graph-captured solves
+    // Event pairs bracketing operator applications (time_kernels): slot 0 the
+    // outer D^+D, slots 1.. the local operators of one preconditioner call.
+    bool time_kernels = false;
+    std::vector<cudaEvent_t> tev;  // 2 per slot
+    std::vector<char> tev_used;
+    void timed_begin(int slot);
+    void timed_end(int slot);
+    // mark slots whose events the stream has been asked to record (direct
+    // launches or graph replays)
+    void timed_mark(int first, int count);
+    // sums elapsed times of the used slots (events must have completed)
+    void timed_collect(double &outer_ms, long long &outer_n, double &local_ms, long long &local_n);
     // per-system activity during a batched solve (device; null outside solves)
     const int *active = nullptr;
     double *ws_d(const std::string &name, size_t n) { return (double *)ws(name, n * sizeof(double)); }
@@ -99,14 +111,16 @@ class Engine {
     // <in, out> from the last stage; returns the CTA tile used.
     // scratch (optional): three caller-provided fields of field_bytes(p, ne, Ls)
     // bytes each, used instead of the engine's workspaces for t1, w, t3.
+    // in_mphi (optional, D and D^+D): M_phi in, precomputed by the producer of
+    // `in`; the first stage then gathers it without applying M_phi on load.
     int apply_global(Prec p, dwf_op op, void *out, const void *in, double *dot_part,
-                     void *const *scratch = nullptr);
+                     void *const *scratch = nullptr, const void *in_mphi = nullptr);
     // Has everything apply_global(p, ...) needs been created already (links,
     // matrices, launch configuration), so that it would allocate nothing?
     bool global_ready(Prec p) const;
     // blocks [b0, b1) only (b1 < 0: all); indices stay absolute
     int apply_local(Prec p, int Ls, void *out, const void *in, double *dot_part, int b0 = 0,
-                    int b1 = -1);
+                    int b1 = -1, const void *in_mphi = nullptr);
     void apply_5d(Prec p, int Ls, MatKind k, void *out, const void *in, long nsite);
 
     // Launch configuration of the hop stages of one operator (0 = global
@@ -147,6 +161,8 @@ struct SolveResult {
     std::vector<double> true_res;
     double ms = 0;
     long long launches = 0;
+    double local_ms = 0, outer_ms = 0;  // with time_kernels
+    long long local_n = 0, outer_n = 0;
 };
 dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dwf_solver_params &p,
                  bool precond, SolveResult &res, std::string &err);

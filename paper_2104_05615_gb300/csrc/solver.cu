@@ -120,8 +120,16 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
     void *pin = E.ws("in_p", field_bytes(pi, n, L));
     void *Apin = E.ws("in_Ap", field_bytes(pi, n, L));
     void *zin = E.ws("in_z", field_bytes(P32, n, L));
+    void *uin = E.ws("in_u", field_bytes(pi, n, L));  // M_phi p, written with p
     double *rr = E.ws_d("in_rr", E.nblk), *al = E.ws_d("in_al", E.nblk), *be = E.ws_d("in_be", E.nblk);
     const uint16_t *tsb = E.seg_blk.d_tile_seg;
+    const double *mphi = E.mats(L).mphi;
+    auto with_u = [&](BlasArgs &a) {
+        a.mphi_out = uin;
+        a.mphi_prec = pi;
+        a.mphi = mphi;
+        if (!a.tile_sys) a.tile_sys = E.tsys_e;
+    };
 
     if (red) launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st);
     // default: every block in one wave (measured fastest on GB300: smaller,
@@ -148,6 +156,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             a.p[1] = red ? pi : po;
             a.v[2] = red ? nullptr : rin;
             a.p[2] = pi;
+            with_u(a);
             launch_blas(BLAS_COPY, a, c.st);
             ScalarArgs t = scal(E.seg_blk, c.part, 1, kBlasTile);
             segs(t);
@@ -162,7 +171,9 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             launch_blas(BLAS_AXPY_ZERO, a, c.st);
         }
         for (int it = 0; it < P.inner_iters; it++) {
-            const int tile = E.apply_local(pi, L, Apin, pin, c.part, b0, b1);
+            E.timed_begin(1 + it);
+            const int tile = E.apply_local(pi, L, Apin, pin, c.part, b0, b1, uin);
+            E.timed_end(1 + it);
             ScalarArgs t = scal(E.seg_blk, c.part, 1, tile);
             segs(t);
             t.s0 = rr;
@@ -187,6 +198,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
                 x.v[0] = pin; x.p[0] = pi;
                 x.v[1] = rin; x.p[1] = pi;
                 x.scal[0] = be;
+                with_u(x);
                 launch_blas(BLAS_XPAY, x, c.st);
             }
         }
@@ -289,6 +301,14 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     void *Ap = E.ws("Ap_o", field_bytes(po, n, Ls));
     void *z = use_precond ? E.ws("z_o", field_bytes(po, n, Ls)) : r;
     void *xacc = po == P64 ? x64 : E.ws("xacc_o", field_bytes(po, n, Ls));
+    void *u = E.ws("u_o", field_bytes(po, n, Ls));  // M_phi p, written with p
+    const double *mphi_o = E.mats(Ls).mphi;
+    auto with_u = [&](BlasArgs &a) {
+        a.mphi_out = u;
+        a.mphi_prec = po;
+        a.mphi = mphi_o;
+        if (!a.tile_sys) a.tile_sys = E.tsys_e;
+    };
     double *bb = E.ws_d("bb", nsys), *rr = E.ws_d("rr", nsys), *rz = E.ws_d("rz", nsys);
     double *al = E.ws_d("al", nsys), *be = E.ws_d("be", nsys), *pAp = E.ws_d("pAp", nsys);
 
@@ -338,14 +358,24 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
         return true;
     };
     int inner_total = 0, ru = 0, iters = 0;
+    // events around every operator application, from the first preconditioner on
+    struct TimeScope {
+        Engine &E;
+        TimeScope(Engine &e, bool on) : E(e) { E.time_kernels = on; }
+        ~TimeScope() { E.time_kernels = false; }
+    } time_scope(E, P.time_kernels != 0 && P.precond_wave == 0);
     bool converged = all_below(h_rr);
 
     // p = z = M^-1 r ; rz = <r, z>
     if (!converged) {
-        if (use_precond) precond_apply(c, po, r, z, inner_total);
+        if (use_precond) {
+            precond_apply(c, po, r, z, inner_total);
+            E.timed_mark(1, P.inner_iters);
+        }
         BlasArgs a = blas(E, n, Ls, E.seg_sys.d_tile_seg, c.part);
         a.v[0] = p; a.p[0] = po;
         a.v[1] = z; a.p[1] = po;
+        with_u(a);
         launch_blas(BLAS_COPY, a, st);  // partial |z|^2 unused
         BlasArgs d = blas(E, n, Ls, nullptr, c.part);
         d.v[0] = r; d.p[0] = po;
@@ -362,7 +392,9 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     double *h_rr_pin = E.pinned_d(nsys);
     auto half1 = [&]() {
         // alpha = <r,z> / <p, Ap> ; x += alpha p ; r -= alpha Ap ; |r|^2 to the host
-        const int tile = E.apply_global(po, DWF_OP_DDAGD, Ap, p, c.part);
+        E.timed_begin(0);
+        const int tile = E.apply_global(po, DWF_OP_DDAGD, Ap, p, c.part, nullptr, u);
+        E.timed_end(0);
         {
             ScalarArgs s = scal(E.seg_sys, c.part, 1, tile);
             s.s0 = rz;
@@ -410,6 +442,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
         x.v[0] = p; x.p[0] = po;
         x.v[1] = z; x.p[1] = po;
         x.scal[0] = be;
+        with_u(x);
         launch_blas(BLAS_XPAY, x, st);
     };
     // per-system activity (batches only): converged systems' CTAs exit at once
@@ -426,11 +459,16 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
         ~ActiveScope() { E.active = nullptr; }
     } active_scope(E, d_active);
     CapturedGraph g1, g2;
+    double t_local = 0, t_outer = 0;
+    long long n_local = 0, n_outer = 0;
     while (!converged && iters < maxiter) {
         const bool graph = P.use_graph && iters > 0;
         g1.run(st, graph, half1);
+        E.timed_mark(0, 1);
         iters++;
         DWF_CUDA(cudaStreamSynchronize(st));
+        // the previous preconditioner call and this outer operator have completed
+        E.timed_collect(t_outer, n_outer, t_local, n_local);
         for (int k = 0; k < nsys; k++) h_rr[k] = h_rr_pin[k];
         for (int k = 0; k < nsys; k++)
             if (!std::isfinite(h_rr[k])) {
@@ -482,6 +520,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             }
         }
         g2.run(st, graph, half2);
+        if (use_precond) E.timed_mark(1, P.inner_iters);
         if (use_precond) inner_total += P.inner_iters;
     }
     // final solution and FP64 true residual (every system)
@@ -512,6 +551,11 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     }
     res.converged = ok;
     res.launches = launch_count() - launches0;
+    E.timed_collect(t_outer, n_outer, t_local, n_local);
+    res.local_ms = t_local;
+    res.local_n = n_local;
+    res.outer_ms = t_outer;
+    res.outer_n = n_outer;
     if (E.check_err()) {
         err = "a bounded device wait gave up";
         return DWF_ETIMEOUT;

@@ -153,3 +153,24 @@ def test_graph_captured_solve_matches_direct_launches(orc):
     assert s1["outer_iters"] == s0["outer_iters"]
     assert torch.equal(x1, x0)
     assert s1["kernel_launches"] == s0["kernel_launches"]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("graph", [0, 1])
+def test_live_operator_timing(orc, graph):
+    """time_kernels: every outer D^+D and every inner local operator of the
+    solve is timed with events on the solve's stream, in graphs too."""
+    from paper_2104_05615_gb300 import binding as B
+    lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st = B.dwf_mspcg(lat.h, x, bd, B.default_params(tol=1e-10, inner_prec=B.DWF_F16, inner_iters=6,
+                                                    use_graph=graph, time_kernels=1))
+    assert st.converged
+    assert st.outer_op_count == st.outer_iters
+    # one preconditioner before the loop and one per iteration that continues
+    assert st.local_op_count == st.inner_iters_total
+    assert st.inner_iters_total >= 6 * st.outer_iters - 6
+    assert 0 < st.outer_op_ms / st.outer_op_count < 50
+    assert 0 < st.local_op_ms / st.local_op_count < 50
+    assert st.local_op_ms < st.time_total_ms
