@@ -227,7 +227,8 @@ typedef struct {
 dwf_status dwf_autotune(dwf_handle *h, dwf_prec prec, int op_kind);
 dwf_status dwf_get_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind, dwf_kernel_config *c);
 /* Fix a configuration (disables autotuning for it).  Rejects choices that do
- * not fit (shared memory, threads, tile not dividing the segment size). */
+ * not fit (shared memory, threads, a tile that does not divide 32, the site
+ * padding of every block and system) with DWF_EINVAL. */
 dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
                                  const dwf_kernel_config *c);
 

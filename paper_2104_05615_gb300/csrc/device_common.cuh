@@ -175,6 +175,25 @@ __device__ __forceinline__ void store_sp<TF16>(void *base, long nsite, long site
     scale_ptr<TF16>(base, nsite, Ls)[(size_t)site * Ls + s] = sc;
 }
 
+// FP16 store of v * f: the values are normalised by max|v| and the stored
+// scale is max|v| * f (the factor never touches the 24 values).
+__device__ __forceinline__ void store_sp_scaled(void *base, long nsite, long site, int s, int Ls,
+                                                const float *v, float f)
+{
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
+    const float sc = m > 0.f ? m : 1.f;
+    const float inv = 1.f / sc;
+    float w[24];
+#pragma unroll
+    for (int i = 0; i < 24; i++) w[i] = v[i] * inv;
+    uint4 *p = reinterpret_cast<uint4 *>(base) + (size_t)site * 3 * Ls + s;
+#pragma unroll
+    for (int c = 0; c < 3; c++) p[(size_t)c * Ls] = pack8(w + 8 * c, __half());
+    scale_ptr<TF16>(base, nsite, Ls)[(size_t)site * Ls + s] = sc * f;
+}
+
 // ---------------------------------------------------------------- links
 // Gathered link rows: [row][8 directions][12 reals] = rows 0 and 1 of the
 // 3x3 complex matrix applied to the neighbour (U_{x,mu} forward,

@@ -30,7 +30,9 @@ bool stage_fits(Prec prec, int tile, int Ls, int gather)
     const bool tma = gather == 1 && prec != P64;
     const StageSmem L = stage_smem(tile, Ls, NC, esz, rsz, tma, tc, prec == P16 && Ls % 4 == 0, true, true);
     const int nthr = (tile * Ls + 31) / 32 * 32;
-    return L.total <= 220 * 1024 && nthr <= 512 && (!tc || (tile * 12) % 8 == 0);
+    // a tile never straddles two kSegPad-aligned segments
+    return L.total <= 220 * 1024 && nthr <= 512 && tile > 0 && kSegPad % tile == 0 &&
+           (!tc || (tile % 4 == 0 && Ls <= 16));  // tensor-core stages pair the n-tiles
 }
 
 }  // namespace dwf

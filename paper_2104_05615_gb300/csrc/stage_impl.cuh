@@ -278,14 +278,39 @@ __device__ __forceinline__ void mma_16816(float *d, const uint4 &a, uint32_t b0,
         : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
+// Four 8x8 FP16 matrices from shared memory, transposed: lane l supplies the
+// address of row (l & 7) of matrix (l >> 3); register i receives matrix i
+// with lane (g, t) holding rows 2t, 2t+1 of column g (an m16n8k16 B fragment).
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                                  uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
 // Shared-memory layout of a stage CTA (byte offsets), shared by host and device.
 struct StageSmem {
     int bar, nbr, smax, lraw, U, mat, col, scl, aux, auxs, dot, dots, H, A, D, total;
 };
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
-__host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz, int rsz, bool tma,
-                                                bool tc, bool scale, bool has_aux, bool has_dot)
+// Tensor-core operand tiles: FP16 [tile][chi][16 slices][kTcRow(TS) halfs],
+// one for h and one for aux; the row pitch is an odd number of 16-byte units
+// so the eight rows of an ldmatrix fall in distinct banks.
+__host__ __device__ constexpr int kTcRow(int TS) { return TS * 12 + 8; }
+// Tensor-core units (chirality x pair of 8-column n-tiles) a warp keeps in
+// registers; with more per warp the FP32 output gets its own buffer.
+constexpr int kTcMaxUnits = 4;
+__host__ __device__ constexpr bool tc_alias(int TS, int Ls)
 {
+    return (TS * 12 / 8 + (TS * Ls + 31) / 32 - 1) / ((TS * Ls + 31) / 32) <= kTcMaxUnits;
+}
+__host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz, int rsz, bool tma,
+                                                bool tc, bool scale, bool has_aux, bool has_dot,
+                                                bool need_ha = true)
+{
+    // need_ha: the FP32 hop / aux buffers H, A (CUDA-core paths and the
+    // bidiagonal S4); the tensor-core stages use the FP16 tiles instead
     StageSmem m;
     const int colb = NC * Ls * 16;
     int o = 0;
@@ -309,27 +334,41 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     o = align16(o + ((tma && has_dot) ? TS * colb : 0));
     m.dots = o;
     o = align16(o + ((tma && has_dot && scale) ? TS * Ls * 4 : 0));
-    // neighbour columns; the hop result H and aux A alias them afterwards
+    // neighbour columns; the hop result (H, A or the FP16 tiles) and the
+    // tensor-core output alias them afterwards
     const int hb = TS * Ls * 24 * rsz;
     m.col = o;
     m.scl = align16(o + (tma ? TS * 8 * colb : 0));
-    const int end_cols = align16(m.scl + ((tma && scale) ? TS * 8 * Ls * 4 : 0));
+    int end = align16(m.scl + ((tma && scale) ? TS * 8 * Ls * 4 : 0));
     m.H = o;
     m.A = align16(m.H + hb);
-    const int end_ha = align16(m.A + (has_aux ? hb : 0));
-    m.D = end_ha;  // tensor-core output when it cannot stay in registers
-    const int end_d = align16(m.D + hb);
-    m.total = end_cols > end_ha ? end_cols : end_ha;
-    // the tensor-core output needs its own buffer only when a warp has more
-    // tiles than it keeps in registers (see the kernel's `alias`)
-    const int nwarp = (TS * Ls + 31) / 32, ntile = TS * 12 / 8;
-    const bool alias = 2 * ((ntile + nwarp - 1) / nwarp) <= 8;
-    if (tc && !alias) m.total = m.total > end_d ? m.total : end_d;
+    m.D = o;
+    if (need_ha) {
+        const int e = align16(m.A + (has_aux ? hb : 0));
+        end = e > end ? e : end;
+    }
+    if (tc) {
+        const int bsz = (has_aux ? 2 : 1) * 2 * 16 * kTcRow(TS) * 2;
+        const int db = TS * Ls * 24 * 4;
+        int e;
+        if (tc_alias(TS, Ls)) {
+            e = align16(o + (bsz > db ? bsz : db));
+        } else {
+            m.D = align16(o + bsz);
+            e = align16(m.D + db);
+        }
+        end = e > end ? e : end;
+    }
+    m.total = end;
     return m;
 }
 
-template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS>
-__global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
+template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS, int TSC>
+// 16-bit stages with precomputed M_phi input are held to 64 registers (two
+// 512-thread blocks' worth per SM): the occupancy gain outweighs the extra
+// rematerialisation.  (M_phi on load needs more live values.)
+__global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi) ? 2 : 1)
+    stage_kernel(const StageArgs a)
 {
     using R = typename T::R;
     constexpr bool kTC = (T::P == P16 || T::P == PB16);
@@ -343,9 +382,11 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
     constexpr bool kH2 = (T::P == P16) && !kMphi && !kTma && (kMode != MODE_5D);
     using LE = typename LinkElem<T>::E;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int Ls = LS > 0 ? LS : a.Ls;  // compile-time for the common fifth extents
-    const int TS = a.tile;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    // compile-time fifth extent and tile for the common shapes
+    const int Ls = LS > 0 ? LS : a.Ls;
+    const int TS = TSC > 0 ? TSC : a.tile;
+    const int tid = threadIdx.x;
+    const int nthr = (LS > 0 && TSC > 0) ? (TSC * LS + 31) / 32 * 32 : (int)blockDim.x;
     const int jl = tid / Ls;
     const int s = tid - jl * Ls;
     const bool active = jl < TS;
@@ -360,7 +401,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
     const bool scale_bulk = kScale && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot);
+                                   has_dot, !kTC || kMode == MODE_S4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
     int *sN = reinterpret_cast<int *>(smem_raw + L.nbr);
     float *sMax = reinterpret_cast<float *>(smem_raw + L.smax);
@@ -372,7 +413,9 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
     const uint4 *sCol = reinterpret_cast<const uint4 *>(smem_raw + L.col);
     const float *sScl = reinterpret_cast<const float *>(smem_raw + L.scl);
 
-    const int seg = (int)i / a.seg_out;
+    // segments are whole multiples of kSegPad sites and TS divides kSegPad:
+    // a CTA never straddles two segments
+    const int seg = (int)i0 / a.seg_out;
     const int loc = (int)i - seg * a.seg_out;
 
     // fifth-dimension matrices for the CUDA-core path, transposed to [t][s][chi]
@@ -398,7 +441,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
         for (int e = tid; e < TS * 8; e += nthr) {
             const int j = e >> 3, k = e & 7;
             const int ii = (int)i0 + j;
-            const int sg_ = ii / a.seg_out, lc = ii - sg_ * a.seg_out;
+            const int sg_ = seg, lc = ii - sg_ * a.seg_out;
             const int nb = __ldg(a.nbr + (long)ii * 8 + k);
             sN[e] = nb;
             uint32_t bytes = 0;
@@ -465,8 +508,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
             for (int e = tid; e < TS * 8; e += nthr) {
                 const int j = e >> 3, k = e & 7;
                 const int ii = (int)i0 + j;
-                const int sg_ = ii / a.seg_out;
-                const long row = (long)sg_ * a.link_stride + (ii - sg_ * a.seg_out);
+                const long row = (long)seg * a.link_stride + (ii - seg * a.seg_out);
                 const int nb = __ldg(a.nbr + (long)ii * 8 + k);
                 sN[e] = nb;
                 R u[18];
@@ -608,14 +650,25 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
         dir(std::integral_constant<int, 7>{});
     }
 
-    // own aux column
+    // own aux column; the S2 tensor-core stage on FP16 storage keeps it as
+    // stored (normalised half values and their scale, which is also their
+    // max-abs) and feeds it to the operand tile in half2 arithmetic
+    constexpr bool kAuxRaw = kTC && kScale && !kTma && kMode == MODE_S2;
     R av[24];
 #pragma unroll
     for (int r = 0; r < 24; r++) av[r] = 0;
+    uint4 araw[3] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+    float asc = 0.f;
     if (kAux) {
         const bool aux_here = (kMode == MODE_S4) || loc < a.aux_valid;
         if (active && aux_here) {
-            if constexpr (kTma) {
+            if constexpr (kAuxRaw) {
+                const long ai = (long)seg * a.aux_stride + loc;
+                const uint4 *ap = reinterpret_cast<const uint4 *>(a.aux) + (size_t)ai * 3 * Ls + s;
+#pragma unroll
+                for (int c = 0; c < 3; c++) araw[c] = __ldg(ap + (size_t)c * Ls);
+                asc = __ldg(scale_ptr<TF16>(a.aux, a.naux, Ls) + (size_t)ai * Ls + s);
+            } else if constexpr (kTma) {
                 decode_chunks<T>(reinterpret_cast<const uint4 *>(smem_raw + L.aux) + jl * (colb / 16) + s, Ls, av);
                 if (kScale) {
                     const float sa = scale_bulk ? reinterpret_cast<const float *>(smem_raw + L.auxs)[jl * Ls + s]
@@ -664,92 +717,143 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
         }
     } else if constexpr (kTC) {
         // ---------------------------------------------------------------
-        // tensor-core path: B = [aux ; h] scaled per site, A = [G | -F] (FP16)
+        // tensor-core path, per chirality D = A . B with A = [G | -F] (FP16
+        // fragments fixed per system; M = output slice, K = input slice) and
+        // B = [aux ; h] (K = slice, N = site x 12 components).  Each site's hop
+        // result and aux column are scaled by their max-abs (Sec. 3.1.4),
+        // written once as FP16 rows of the B tiles and read back as fragments
+        // with ldmatrix.trans; D is rescaled by the same factor.
+        const int RS = kTcRow(TS);
+        constexpr int nk = kAux ? 2 : 1;
+        __half *sB = reinterpret_cast<__half *>(smem_raw + L.H);
         if (active) {
             float m = 0.f;
-            store24(sH + (jl * Ls + s) * 24, acc);
 #pragma unroll
             for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(acc[r]));
-            if (kAux) {
-                store24(sA + (jl * Ls + s) * 24, av);
+            if constexpr (kAuxRaw) {
+                m = fmaxf(m, asc);
+            } else if constexpr (kAux) {
 #pragma unroll
                 for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(av[r]));
             }
             atomicMax(reinterpret_cast<int *>(sMax + jl), __float_as_int(m));
         }
+        {
+            // slices Ls..15 of every tile are zero (K padded to 16)
+            const int padq = (16 - Ls) * RS / 8;
+            for (int e = tid; e < nk * 2 * padq; e += nthr) {
+                const int tl = e / padq, q = e - tl * padq;
+                reinterpret_cast<uint4 *>(sB + ((size_t)tl * 16 + Ls) * RS)[q] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const float sig = sMax[jl];
+            const float inv = sig > 0.f ? 1.f / sig : 0.f;
+            auto put = [&](__half *tile, const R *v) {
+#pragma unroll
+                for (int chi = 0; chi < 2; chi++) {
+                    uint2 *dst = reinterpret_cast<uint2 *>(tile + ((size_t)chi * 16 + s) * RS + jl * 12);
+#pragma unroll
+                    for (int q = 0; q < 3; q++) {
+                        const R *w = v + chi * 12 + 4 * q;
+                        dst[q] = make_uint2(pack_h2(w[0] * inv, w[1] * inv), pack_h2(w[2] * inv, w[3] * inv));
+                    }
+                }
+            };
+            // tile 0: aux (if any) else h ; tile 1: h
+            if constexpr (kAuxRaw) {
+                // stored halves times (aux scale / site scale) <= 1
+                const __half2 r2 = __float2half2_rn(asc * inv);
+                auto mul = [&](uint32_t w) {
+                    __half2 h = *reinterpret_cast<const __half2 *>(&w);
+                    h = __hmul2(h, r2);
+                    return *reinterpret_cast<uint32_t *>(&h);
+                };
+                // chirality 0 = halves 0..11, chirality 1 = halves 12..23
+                uint2 *d0 = reinterpret_cast<uint2 *>(sB + (size_t)s * RS + jl * 12);
+                uint2 *d1 = reinterpret_cast<uint2 *>(sB + ((size_t)16 + s) * RS + jl * 12);
+                d0[0] = make_uint2(mul(araw[0].x), mul(araw[0].y));
+                d0[1] = make_uint2(mul(araw[0].z), mul(araw[0].w));
+                d0[2] = make_uint2(mul(araw[1].x), mul(araw[1].y));
+                d1[0] = make_uint2(mul(araw[1].z), mul(araw[1].w));
+                d1[1] = make_uint2(mul(araw[2].x), mul(araw[2].y));
+                d1[2] = make_uint2(mul(araw[2].z), mul(araw[2].w));
+                put(sB + (size_t)2 * 16 * RS, acc);
+            } else if (kAux) {
+                put(sB, av);
+                put(sB + (size_t)2 * 16 * RS, acc);
+            } else {
+                put(sB, acc);
+            }
+        }
         __syncthreads();
         const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
         const int g = lane >> 2, tg = lane & 3;
-        const int ntile = TS * 12 / 8;  // n-tiles per chirality
-        constexpr int nk = kAux ? 2 : 1;
+        const int npair = TS * 12 / 16;  // pairs of 8-column n-tiles per chirality
+        const int nunit = 2 * npair;
         const uint4 *Af = reinterpret_cast<const uint4 *>(a.F) + (size_t)sys * 2 * 2 * 32;
-        // results stay in registers (up to kMaxT tiles per warp) so that the
-        // output tile can overwrite sH; otherwise they go to a separate buffer
-        constexpr int kMaxT = 8;
-        const bool alias = 2 * ((ntile + nwarp - 1) / nwarp) <= kMaxT;
-        R *sD = alias ? sH : reinterpret_cast<R *>(smem_raw + L.D);
-        float dreg[kMaxT][4];
-        // A fragments of this lane: [chi][k-step]
-        uint4 af[2][2];
+        uint4 af[2][2];  // A fragments of this lane: [chi][k-step]
 #pragma unroll
         for (int chi = 0; chi < 2; chi++)
 #pragma unroll
             for (int kk = 0; kk < nk; kk++) af[chi][kk] = __ldg(Af + ((chi * 2 + kk) * 32 + lane));
-        const int t0 = 2 * tg, t1 = 2 * tg + 8;
-        const bool v0 = t0 < Ls, v1 = t0 + 1 < Ls, v2 = t1 < Ls, v3 = t1 + 1 < Ls;
-        auto tile_mma = [&](int chi, int nt, float *d) {
-            const int n = nt * 8 + g;  // this lane's B column
-            const int jb = n / 12, rb = chi * 12 + (n - jb * 12);
-            const float sig = sMax[jb];
-            const float inv = sig > 0.f ? 1.f / sig : 0.f;
-            d[0] = d[1] = d[2] = d[3] = 0.f;
+        // this lane's ldmatrix row: slice lr of n-tile ln / 8 of the pair
+        const int lr = (lane & 7) + 8 * ((lane >> 3) & 1);
+        const int ln = 8 * (lane >> 4);
+        const bool alias = tc_alias(TS, Ls);
+        R *sD = reinterpret_cast<R *>(smem_raw + L.D);
+        auto unit_mma = [&](int u, float *d) {
+            const int chi = u / npair, pr = u - chi * npair;
+#pragma unroll
+            for (int q = 0; q < 8; q++) d[q] = 0.f;
 #pragma unroll
             for (int kk = 0; kk < nk; kk++) {
-                // kk = 0: aux (if any) else h ; kk = 1: h
-                const R *colp = ((kAux && kk == 0) ? sA : sH) + (jb * Ls) * 24 + rb;
-                const float x0 = v0 ? colp[t0 * 24] * inv : 0.f;
-                const float x1 = v1 ? colp[(t0 + 1) * 24] * inv : 0.f;
-                const float x2 = v2 ? colp[t1 * 24] * inv : 0.f;
-                const float x3 = v3 ? colp[(t1 + 1) * 24] * inv : 0.f;
-                mma_16816(d, af[chi][kk], pack_h2(x0, x1), pack_h2(x2, x3));
+                const __half *tb = sB + ((size_t)(kk * 2 + chi) * 16 + lr) * RS + pr * 16 + ln;
+                uint32_t b0, b1, b2, b3;
+                ldmatrix_x4_trans(smem_u32(tb), b0, b1, b2, b3);
+                mma_16816(d, af[chi][kk], b0, b1);
+                mma_16816(d + 4, af[chi][kk], b2, b3);
             }
         };
-        auto tile_store = [&](int chi, int nt, const float *d) {
-            // D rows s = g, g + 8 ; columns nt*8 + 2 tg, +1 -> same site
-            const int nd = nt * 8 + 2 * tg;
-            const int jd = nd / 12, rd = chi * 12 + (nd - jd * 12);
-            const float sd = sMax[jd];
-            if (g < Ls)
-                *reinterpret_cast<float2 *>(sD + (jd * Ls + g) * 24 + rd) = make_float2(d[0] * sd, d[1] * sd);
-            if (g + 8 < Ls)
-                *reinterpret_cast<float2 *>(sD + (jd * Ls + g + 8) * 24 + rd) = make_float2(d[2] * sd, d[3] * sd);
+        auto unit_store = [&](int u, const float *d) {
+            // D rows s = g, g + 8 ; columns 2 tg, 2 tg + 1 of each n-tile -> one site
+            const int chi = u / npair, pr = u - chi * npair;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int nd = pr * 16 + h * 8 + 2 * tg;
+                const int jd = nd / 12, rd = chi * 12 + (nd - jd * 12);
+                // FP16 storage folds the site scale into the stored scale
+                const float sd = kScale ? 1.f : sMax[jd];
+                if (g < Ls)
+                    *reinterpret_cast<float2 *>(sD + (jd * Ls + g) * 24 + rd) =
+                        make_float2(d[4 * h] * sd, d[4 * h + 1] * sd);
+                if (g + 8 < Ls)
+                    *reinterpret_cast<float2 *>(sD + (jd * Ls + g + 8) * 24 + rd) =
+                        make_float2(d[4 * h + 2] * sd, d[4 * h + 3] * sd);
+            }
         };
         if (alias) {
-            // tiles of this warp: nt = warp + u * nwarp for each chirality
-            constexpr int kHalf = kMaxT / 2;
+            // the units of this warp stay in registers while the output
+            // overwrites the operand tiles
+            float dreg[kTcMaxUnits][8];
 #pragma unroll
-            for (int chi = 0; chi < 2; chi++)
+            for (int u = 0; u < kTcMaxUnits; u++) {
+                const int uu = warp + u * nwarp;
+                if (uu < nunit) unit_mma(uu, dreg[u]);
+            }
+            __syncthreads();  // every warp has read the tiles
 #pragma unroll
-                for (int u = 0; u < kHalf; u++) {
-                    const int nt = warp + u * nwarp;
-                    if (nt < ntile) tile_mma(chi, nt, dreg[chi * kHalf + u]);
-                }
-            __syncthreads();  // every warp has read sH / sA
-#pragma unroll
-            for (int chi = 0; chi < 2; chi++)
-#pragma unroll
-                for (int u = 0; u < kHalf; u++) {
-                    const int nt = warp + u * nwarp;
-                    if (nt < ntile) tile_store(chi, nt, dreg[chi * kHalf + u]);
-                }
+            for (int u = 0; u < kTcMaxUnits; u++) {
+                const int uu = warp + u * nwarp;
+                if (uu < nunit) unit_store(uu, dreg[u]);
+            }
         } else {
-#pragma unroll
-            for (int chi = 0; chi < 2; chi++)
-                for (int nt = warp; nt < ntile; nt += nwarp) {
-                    float d[4];
-                    tile_mma(chi, nt, d);
-                    tile_store(chi, nt, d);
-                }
+            for (int uu = warp; uu < nunit; uu += nwarp) {
+                float d[8];
+                unit_mma(uu, d);
+                unit_store(uu, d);
+            }
         }
         __syncthreads();
         if (active) {
@@ -789,7 +893,12 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
         }
     }
 
-    if (active) store_sp<T>(a.out, a.nout, i, s, Ls, out);
+    if constexpr (kTC && kScale && kMode != MODE_S4) {
+        // out holds D / (site scale): the factor goes into the stored scale
+        if (active) store_sp_scaled(a.out, a.nout, i, s, Ls, out, sMax[jl]);
+    } else {
+        if (active) store_sp<T>(a.out, a.nout, i, s, Ls, out);
+    }
 
     if (kMode == MODE_S4 && a.dot_part) {
         // partial <dotv, out> (real part), per thread in R, across threads in FP64
@@ -825,7 +934,7 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs a)
     }
 }
 
-template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS>
+template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS, int TSC>
 static void launch_t(const StageArgs &a, cudaStream_t st)
 {
     using R = typename T::R;
@@ -838,53 +947,60 @@ static void launch_t(const StageArgs &a, cudaStream_t st)
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
     const bool scale_bulk = (T::P == P16) && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, T::NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot);
+                                   has_dot, !kTC || kMode == MODE_S4);
     static bool attr_set = false;
     if (!attr_set) {
-        DWF_CUDA(cudaFuncSetAttribute(stage_kernel<T, kMode, kMphi, kStage, kDag, LS>,
+        DWF_CUDA(cudaFuncSetAttribute(stage_kernel<T, kMode, kMphi, kStage, kDag, LS, TSC>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
         attr_set = true;
     }
     if (L.total > 220 * 1024) throw std::runtime_error("stage tile does not fit in shared memory");
     const long nblk = a.nout / TS;
-    stage_kernel<T, kMode, kMphi, kStage, kDag, LS><<<(unsigned)nblk, nthr, L.total, st>>>(a);
+    stage_kernel<T, kMode, kMphi, kStage, kDag, LS, TSC><<<(unsigned)nblk, nthr, L.total, st>>>(a);
     DWF_CUDA(cudaGetLastError());
     count_launch();
 }
 
-template <class T, bool kStage, int LS>
+template <class T, bool kStage, int LS, int TSC>
 static void dispatch_mode(StageMode mode, bool mphi, const StageArgs &a, cudaStream_t st)
 {
     // the combinations the operators use: S1 (F, M_phi), S2, S3 (F, dagger),
     // S4 (dagger), and the fifth-dimension-only products
-    if (mode == MODE_F && mphi && !a.dagger) launch_t<T, MODE_F, true, kStage, false, LS>(a, st);
-    else if (mode == MODE_F && !mphi && a.dagger) launch_t<T, MODE_F, false, kStage, true, LS>(a, st);
-    else if (mode == MODE_F && !mphi && !a.dagger) launch_t<T, MODE_F, false, kStage, false, LS>(a, st);
-    else if (mode == MODE_S2 && !mphi && !a.dagger) launch_t<T, MODE_S2, false, kStage, false, LS>(a, st);
-    else if (mode == MODE_S4 && !mphi && a.dagger) launch_t<T, MODE_S4, false, kStage, true, LS>(a, st);
-    else if (mode == MODE_5D) launch_t<T, MODE_5D, false, false, false, LS>(a, st);
+    if (mode == MODE_F && mphi && !a.dagger) launch_t<T, MODE_F, true, kStage, false, LS, TSC>(a, st);
+    else if (mode == MODE_F && !mphi && a.dagger) launch_t<T, MODE_F, false, kStage, true, LS, TSC>(a, st);
+    else if (mode == MODE_F && !mphi && !a.dagger) launch_t<T, MODE_F, false, kStage, false, LS, TSC>(a, st);
+    else if (mode == MODE_S2 && !mphi && !a.dagger) launch_t<T, MODE_S2, false, kStage, false, LS, TSC>(a, st);
+    else if (mode == MODE_S4 && !mphi && a.dagger) launch_t<T, MODE_S4, false, kStage, true, LS, TSC>(a, st);
+    else if (mode == MODE_5D) launch_t<T, MODE_5D, false, false, false, LS, TSC>(a, st);
     else throw std::runtime_error("unsupported stage combination");
 }
 
 // Per-precision entry: compile-time fifth extent for Ls in {4, 8, 12, 16}
-// with direct gathers; every other case (and bulk-copy gathers) uses the
-// runtime-Ls kernel.
+// with direct gathers, and a compile-time 8-site tile for Ls 12 and 16 (the
+// tile the autotuner picks on GB300); every other case (and bulk-copy
+// gathers) uses the runtime-Ls, runtime-tile kernel.
 template <class T>
 void launch_stage_prec(StageMode mode, bool mphi, const StageArgs &a, cudaStream_t st)
 {
     if (a.gather == 1 && T::P != P64) {
-        dispatch_mode<T, true, 0>(mode, mphi, a, st);
+        dispatch_mode<T, true, 0, 0>(mode, mphi, a, st);
         return;
     }
     if constexpr (T::P == P64) {
-        dispatch_mode<T, false, 0>(mode, mphi, a, st);
+        dispatch_mode<T, false, 0, 0>(mode, mphi, a, st);
     } else {
         switch (a.Ls) {
-        case 4: dispatch_mode<T, false, 4>(mode, mphi, a, st); break;
-        case 8: dispatch_mode<T, false, 8>(mode, mphi, a, st); break;
-        case 12: dispatch_mode<T, false, 12>(mode, mphi, a, st); break;
-        case 16: dispatch_mode<T, false, 16>(mode, mphi, a, st); break;
-        default: dispatch_mode<T, false, 0>(mode, mphi, a, st); break;
+        case 4: dispatch_mode<T, false, 4, 0>(mode, mphi, a, st); break;
+        case 8: dispatch_mode<T, false, 8, 0>(mode, mphi, a, st); break;
+        case 12:
+            if (a.tile == 8) dispatch_mode<T, false, 12, 8>(mode, mphi, a, st);
+            else dispatch_mode<T, false, 12, 0>(mode, mphi, a, st);
+            break;
+        case 16:
+            if (a.tile == 8) dispatch_mode<T, false, 16, 8>(mode, mphi, a, st);
+            else dispatch_mode<T, false, 16, 0>(mode, mphi, a, st);
+            break;
+        default: dispatch_mode<T, false, 0, 0>(mode, mphi, a, st); break;
         }
     }
 }
