@@ -398,31 +398,18 @@ def main():
 
     import torch
     from paper_2104_05615_gb300 import build as _build
+    from paper_2104_05615_gb300.replicas import Replicas
     _build.build()
     torch.cuda.set_device(local_rank)
     device = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=device)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def maxall(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    rep = Replicas("nccl", device)  # independent replicas: host-side barrier and max only
+    barrier, maxall = rep.barrier, rep.max
 
     from paper_2104_05615_gb300 import binding as B
     cfg_name = args.config
     if cfg_name == "C5":
         run_batch(args, device, rank, world, barrier, maxall)
-        if dist is not None:
-            dist.destroy_process_group()
+        rep.close()
         return
     cfg, lat, b, bd = setup(cfg_name, device)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
@@ -588,8 +575,7 @@ def main():
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
                 "roofline": roofline, "dslash": dslash, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
 
 
 if __name__ == "__main__":
