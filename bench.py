@@ -380,8 +380,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves"],
-                    help="ops: only apply the operators (for profilers)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves", "inner"],
+                    help="ops: only apply the operators (for profilers); inner: outer iterations "
+                         "and time to solution against the inner iteration count and precision")
     ap.add_argument("--op-reps", type=int, default=3)
     ap.add_argument("--kcfg", default=None,
                     help="fixed stage launch config 'tile,gather' for both operators (ops mode)")
@@ -426,6 +427,40 @@ def main():
         tg = time_op(lat, B.DWF_OP_DDAGD, "f32", args.op_reps, flush)
         if rank == 0:
             print(json.dumps({"local_ms": tl * 1e3, "global_ms": tg * 1e3}))
+        return
+    if args.mode == "inner":
+        # Table 1's trend on this workload: plain CG, then MSPCG with k inner
+        # iterations in FP16 and BF16 (one warm-up and one timed solve each)
+        from paper_2104_05615_gb300.lattice import PREC
+        rows = []
+        runs = [("plain", None, 0)] + [(k, pr, 0) for pr in ("f16", "bf16") for k in (3, 4, 6, 12, 18)]
+        runs.append((6, "f16", 1))  # the snake-term ablation (Eq. (eq:diri))
+        for k, pr, trunc in runs:
+            B.dwf_set_local_truncated(lat.h, trunc)
+            if k == "plain":
+                p = solver_params(cfg, False)
+            else:
+                p = solver_params(cfg, True)
+                p.inner_iters = k
+                p.inner_prec = PREC[pr]
+            fn = B.dwf_cg if k == "plain" else B.dwf_mspcg
+            x = torch.zeros_like(bd)
+            fn(lat.h, x, bd, p)
+            x.zero_()
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = fn(lat.h, x, bd, p, raise_on_noconv=False)
+            e1.record()
+            e1.synchronize()
+            rows.append({"inner_iters": k, "inner_prec": pr, "truncated_local_op": bool(trunc),
+                         "outer_iters": st.outer_iters,
+                         "inner_iters_total": st.inner_iters_total, "reliable_updates": st.reliable_updates,
+                         "seconds": e0.elapsed_time(e1) / 1000.0, "true_residual": st.true_residual})
+            if rank == 0:
+                print(json.dumps(rows[-1]), flush=True)
+        B.dwf_set_local_truncated(lat.h, 0)
         return
     if args.mode == "waves":
         # the preconditioner alone (FP64 canonical in/out) for several wave sizes

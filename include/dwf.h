@@ -180,6 +180,17 @@ dwf_status dwf_precondition(dwf_handle *h, double *z_dev, const double *r_dev,
  * row index s*4 + spin, column index t*4 + spin; trivial in colour. */
 dwf_status dwf_set_reduced_ls(dwf_handle *h, int Ls_hat, const double *T_host, double mu);
 
+/* Ablation of the snake terms (Sec. 2.3, Eq. (eq:diri)): with on != 0 every
+ * later use of the local operator A_s on this handle (dwf_apply with
+ * DWF_OP_LOCAL_DDAGD, dwf_precondition, dwf_mspcg) applies Dirichlet walls at
+ * the block boundary on each of the four hops of D^+D instead of restricting
+ * the full D^+D to the block, i.e. the truncated product on the left of
+ * Eq. (eq:diri).  on = 0 restores A_s = R_s D^+D R_s^T.  The first call with
+ * on != 0 builds the filtered neighbour tables on the device (DWF_ENOMEM or
+ * DWF_ECUDA on failure).  Not part of the method: it exists to measure what
+ * the snake terms buy. */
+dwf_status dwf_set_local_truncated(dwf_handle *h, int on);
+
 /* Batched MSPCG over independent lattices (uneven sizes allowed; same Ls,
  * b, c, M5 and block dims; per-lattice mass and gauge field).  The handles
  * stay owned by the caller and must outlive the batch. */

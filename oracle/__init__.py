@@ -182,6 +182,52 @@ class Oracle:
                                         C.c_long(block), _ptr(x), _ptr(out))
         return out
 
+    def block_mask(self, sub, block, par):
+        """1 on the sites of checkerboard `par` (cb index lex // 2) that lie in
+        block `block` (numbered as block_ids), else 0; shape (Vh,)."""
+        nb = [self.dims[mu] // sub[mu] for mu in range(4)]
+        m = np.zeros(self.Vh)
+        for lex in range(self.V):
+            x, t = [], lex
+            for mu in range(4):
+                x.append(t % self.dims[mu])
+                t //= self.dims[mu]
+            if sum(x) % 2 != par:
+                continue
+            b = x[0] // sub[0] + nb[0] * (x[1] // sub[1] + nb[1] * (x[2] // sub[2] + nb[2] * (x[3] // sub[3])))
+            if b == block:
+                m[lex // 2] = 1.0
+        return m
+
+    def local_DdagD_truncated(self, x, sub, block=None):
+        """The left side of Eq. (eq:diri): D^+D with Dirichlet walls at the
+        block boundary on each of its four hops (Sec. 2.3; the snake terms that
+        leave the block and come back are dropped), on the block's even sites:
+        P_e D_t^+ D_t P_e with D_t = 1 - M5^-1 P_e M4_eo P_o M5^-1 P_o M4_oe P_e.
+        block None: the sum over all blocks."""
+        x = _c(x).reshape(self.cb_shape())
+        if block is None:
+            nblk = int(np.prod([self.dims[mu] // sub[mu] for mu in range(4)]))
+            return sum(self.local_DdagD_truncated(x, sub, b) for b in range(nblk))
+        Pe = self.block_mask(sub, block, 0)[None, :, None, None]
+        Po = self.block_mask(sub, block, 1)[None, :, None, None]
+        Mi = self.matrix5(M5INV)
+        Mid = Mi.conj().T
+
+        def Dt(v):
+            k = self.m4(Pe * v, 0)                     # M4_oe: even -> odd
+            k = self.apply5(Mi, Po * k)
+            k = self.m4(Po * k, 1)                     # M4_eo: odd -> even
+            return v - self.apply5(Mi, Pe * k)
+
+        def Dt_dag(v):
+            k = Pe * self.apply5(Mid, v)
+            k = Po * self.m4(k, 0, dagger=True)        # M4_eo^+: even -> odd
+            k = Po * self.apply5(Mid, k)
+            return v - Pe * self.m4(k, 1, dagger=True)  # M4_oe^+: odd -> even
+
+        return Pe * Dt_dag(Dt(Pe * x))
+
     def T_apply(self, T, x, Ls_hat, dagger=False):
         x = _c(x)
         nsite = x.shape[1]

@@ -81,6 +81,7 @@ def lib() -> C.CDLL:
                                    C.POINTER(dwf_stats)]),
             "dwf_precondition": (i, [vp, vp, vp, C.POINTER(dwf_solver_params)]),
             "dwf_set_reduced_ls": (i, [vp, i, vp, d]),
+            "dwf_set_local_truncated": (i, [vp, i]),
             "dwf_batch_create": (i, [C.POINTER(vp), C.POINTER(vp), i]),
             "dwf_batch_destroy": (None, [vp]),
             "dwf_batch_mspcg": (i, [vp, C.POINTER(vp), C.POINTER(vp),
@@ -231,6 +232,10 @@ def dwf_precondition(h, z, r, params=None):
 
 def dwf_set_reduced_ls(h, Ls_hat, T_host, mu):
     return check(lib().dwf_set_reduced_ls(h, int(Ls_hat), _ptr(T_host), float(mu)), h)
+
+
+def dwf_set_local_truncated(h, on):
+    return check(lib().dwf_set_local_truncated(h, int(bool(on))), h)
 
 
 def dwf_batch_create(handles):

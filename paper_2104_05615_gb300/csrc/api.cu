@@ -320,6 +320,15 @@ dwf_status dwf_set_reduced_ls(dwf_handle *h, int Ls_hat, const double *T_host, d
     });
 }
 
+dwf_status dwf_set_local_truncated(dwf_handle *h, int on)
+{
+    if (!h) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        h->E->set_local_truncated(on != 0);
+        return DWF_OK;
+    });
+}
+
 dwf_status dwf_batch_create(dwf_batch **out, dwf_handle *const *hs, int n)
 {
     if (!out || !hs || n < 1) return DWF_EINVAL;

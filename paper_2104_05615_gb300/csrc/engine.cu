@@ -10,6 +10,57 @@
 
 namespace dwf {
 
+// Local stage tables of all systems, concatenated with block offsets.  With
+// dirichlet, only hops between sites inside the block are kept: the four hops
+// of D^+D then each see Dirichlet walls at the block boundary, the left side
+// of Eq. (eq:diri) (the snake terms dropped; outputs outside the block are 0).
+void Engine::local_tables(std::vector<int> *h, bool dirichlet) const
+{
+    const int Nb = sys[0].g->Nb;  // every system has the same block shape
+    auto inside = [](int e, int pad, int nb) {
+        const long idx = e >= 0 ? (long)e : (long)(-e - 2);
+        return idx % pad < nb;
+    };
+    auto add = [&](std::vector<int> &dst, const std::vector<int> &src, long off, int out_pad, int in_pad) {
+        const long rows = (long)src.size() / 8;
+        for (long r = 0; r < rows; r++) {
+            const bool out_in = (r % out_pad) < Nb;
+            for (int k = 0; k < 8; k++) {
+                const int e = src[r * 8 + k];
+                if (e == -1 || (dirichlet && (!out_in || !inside(e, in_pad, Nb)))) {
+                    dst.push_back(-1);
+                } else if (e >= 0) {
+                    dst.push_back((int)(e + off));
+                } else {
+                    dst.push_back((int)(-(((long)-e - 2) + off) - 2));
+                }
+            }
+        }
+    };
+    for (int k = 0; k < 4; k++) h[k].clear();
+    for (auto &sy : sys) {
+        const LatticeGeom &g = *sy.g;
+        const long bo = sy.blk_off;
+        add(h[0], g.t1, bo * Nb_pad, O1_pad, Nb_pad);  // O1 <- interior
+        add(h[1], g.t2, bo * O1_pad, E2_pad, O1_pad);  // E2 <- O1
+        add(h[2], g.t3, bo * E2_pad, O1_pad, E2_pad);  // O1 <- E2
+        add(h[3], g.t4, bo * O1_pad, Nb_pad, O1_pad);  // interior <- O1
+    }
+}
+
+void Engine::set_local_truncated(bool on)
+{
+    if (on && !td1) {
+        std::vector<int> h[4];
+        local_tables(h, true);
+        td1 = upload(h[0]);
+        td2 = upload(h[1]);
+        td3 = upload(h[2]);
+        td4 = upload(h[3]);
+    }
+    local_truncated = on;
+}
+
 // Under stream capture the record must be an external event node, so that
 // every replay of the graph re-records the event; outside capture the flag is
 // refused and a plain record is taken.
@@ -152,22 +203,21 @@ void Engine::init(const std::vector<SysInfo> &sysv, int Ls_, double b_, double c
             else dst.push_back((int)(-(((long)-e - 2) + off) - 2));
         }
     };
-    std::vector<int> he, ho, h1, h2, h3, h4;
+    std::vector<int> he, ho;
     for (auto &s : sys) {
-        const LatticeGeom &g = *s.g;
-        shift(he, g.nbr_e, s.off);
-        shift(ho, g.nbr_o, s.off);
-        shift(h1, g.t1, (long)s.blk_off * Nb_pad);
-        shift(h2, g.t2, (long)s.blk_off * O1_pad);
-        shift(h3, g.t3, (long)s.blk_off * E2_pad);
-        shift(h4, g.t4, (long)s.blk_off * O1_pad);
+        shift(he, s.g->nbr_e, s.off);
+        shift(ho, s.g->nbr_o, s.off);
     }
     nbr_e = upload(he);
     nbr_o = upload(ho);
-    t1 = upload(h1);
-    t2 = upload(h2);
-    t3 = upload(h3);
-    t4 = upload(h4);
+    {
+        std::vector<int> h[4];
+        local_tables(h, false);
+        t1 = upload(h[0]);
+        t2 = upload(h[1]);
+        t3 = upload(h[2]);
+        t4 = upload(h[3]);
+    }
 
     // per-tile system ids (only needed for several systems)
     if (sys.size() > 1) {
@@ -607,7 +657,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     a.nin = nI;
     a.out = t1v;
     a.nout = nO1;
-    a.nbr = t1;
+    a.nbr = local_truncated ? td1 : t1;
     a.links = links(2, p);
     a.tile_sys = tsys_O1;
     a.seg_out = O1_pad;
@@ -628,7 +678,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b2.nin = nO1;
     b2.out = wv;
     b2.nout = nE2;
-    b2.nbr = t2;
+    b2.nbr = local_truncated ? td2 : t2;
     b2.links = links(3, p);
     b2.tile_sys = tsys_E2;
     b2.seg_out = E2_pad;
@@ -652,7 +702,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b3.nin = nE2;
     b3.out = t3v;
     b3.nout = nO1;
-    b3.nbr = t3;
+    b3.nbr = local_truncated ? td3 : t3;
     b3.links = links(2, p);
     b3.tile_sys = tsys_O1;
     b3.seg_out = O1_pad;
@@ -673,7 +723,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b4.nin = nO1;
     b4.out = out;
     b4.nout = nI;
-    b4.nbr = t4;
+    b4.nbr = local_truncated ? td4 : t4;
     b4.links = links(3, p);
     b4.tile_sys = tsys_e;
     b4.seg_out = Nb_pad;

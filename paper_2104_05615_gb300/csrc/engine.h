@@ -75,6 +75,12 @@ class Engine {
     // device tables
     int *nbr_e = nullptr, *nbr_o = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr,
         *t4 = nullptr;
+    // the local operator with Dirichlet walls on each hop (Eq. (eq:diri),
+    // left side; an ablation of the snake terms), built on first use
+    int *td1 = nullptr, *td2 = nullptr, *td3 = nullptr, *td4 = nullptr;
+    bool local_truncated = false;
+    void set_local_truncated(bool on);
+    void local_tables(std::vector<int> *h, bool dirichlet) const;
     uint16_t *tsys_e = nullptr, *tsys_O1 = nullptr, *tsys_E2 = nullptr;  // null for 1 system
     Seg seg_sys, seg_blk;
     std::vector<long *> perm;  // per system: packed -> canonical cb (device)

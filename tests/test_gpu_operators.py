@@ -102,3 +102,26 @@ def test_invalid_arguments_rejected():
         B.dwf_create(U, (4, 4, 4, 4), 8, 1.5, 0.5, 1.8, 0.1, (2, 4, 4, 4))
     with pytest.raises(B.DwfError):   # block does not divide
         B.dwf_create(U, (4, 4, 4, 4), 8, 1.5, 0.5, 1.8, 0.1, (6, 4, 4, 4))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["part_x", "ragged_part", "ls16_4d"])
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_truncated_local_operator(orc, name, prec):
+    """dwf_set_local_truncated: the local operator with Dirichlet walls on every
+    hop (the left side of Eq. (eq:diri)) against the oracle's truncated
+    product; switching back gives R_s D^+D R_s^T again."""
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import to_device, to_numpy
+    lat, o, x, sub = setup_case(orc, name)
+    xd = to_device(x, prec)
+    xin = to_numpy(xd)
+    want_t = o.local_DdagD_truncated(xin, sub)
+    want_s = o.local_DdagD(xin, sub)
+    assert relerr(want_t, want_s) > 1e-3  # the snake terms matter here
+    B.dwf_set_local_truncated(lat.h, 1)
+    e = relerr(to_numpy(lat.apply("local", xd, prec)), want_t)
+    assert e < TOL[prec], f"truncated {name} {prec}: {e:.3e}"
+    B.dwf_set_local_truncated(lat.h, 0)
+    e = relerr(to_numpy(lat.apply("local", xd, prec)), want_s)
+    assert e < TOL[prec], f"snake {name} {prec}: {e:.3e}"

@@ -291,6 +291,11 @@ def test_local_operator_snake_terms(orc):
     # the sequentially truncated product (Dirichlet on every hop) is different
     A_trunc = _padded_local(o, dims, Ls, sub, origin, 0)
     assert np.abs(A_loc - A_trunc).max() > 1e-3
+    # the oracle's truncated operator (vector form) is that dense product
+    A_tr = dense_of(lambda v: o.local_DdagD_truncated(v, sub, block=blk), o.cb_shape())
+    np.testing.assert_allclose(A_tr, A_trunc, atol=1e-12)
+    # its even block mask agrees with block_ids
+    np.testing.assert_array_equal(o.block_mask(sub, blk, 0) > 0, bid == blk)
     # and a pad of one is not enough to capture every snake
     A_pad1 = _padded_local(o, dims, Ls, sub, origin, 1)
     assert np.abs(A_loc - A_pad1).max() > 1e-4
