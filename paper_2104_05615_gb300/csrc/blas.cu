@@ -106,15 +106,19 @@ __device__ __forceinline__ void block_reduce_store(double v0, double v1, int nco
     }
 }
 
-// One thread per 5D site (site, s); a CTA covers `tile` sites x Ls.
-template <typename R>
-__global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
+// One thread per 5D site (site, s); a CTA covers `tile` sites x Ls.  One
+// instantiation per operation, so that each keeps only its own operands live:
+// the single-precision instances stay within 64 registers (several CTAs per
+// SM keep enough loads in flight for HBM).
+template <typename R, int OP>
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasArgs a)
 {
     const int Ls = a.Ls;
     const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
     const long i = a.site0 + (long)blockIdx.x * a.tile + jl;
     const long cta = a.site0 / a.tile + blockIdx.x;  // absolute CTA index (partials)
     const bool active = jl < a.tile && i < (a.site_end ? a.site_end : a.nsite);
+    constexpr int ncomp = OP == BLAS_DOT2 ? 2 : 1;
     double p0 = 0, p1 = 0;
     const int seg = (active && a.tile_seg) ? a.tile_seg[i / kSegPad] : 0;
     const long n = a.nsite;
@@ -123,72 +127,78 @@ __global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
         const long i0 = a.site0 + (long)blockIdx.x * a.tile;
         const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
         if (!a.active[sys]) {
-            if (a.part && threadIdx.x == 0) {
-                const int nc = op == BLAS_DOT2 ? 2 : 1;
-                for (int c = 0; c < nc; c++) a.part[(size_t)cta * nc + c] = 0.0;
-            }
+            if (a.part && threadIdx.x == 0)
+                for (int c = 0; c < ncomp; c++) a.part[(size_t)cta * ncomp + c] = 0.0;
             return;
         }
     }
     if (active) {
-        R v0[24], v1[24], v2[24], v3[24];
-        switch (op) {
-        case BLAS_DOT:
-        case BLAS_DOT2: {
+        if constexpr (OP == BLAS_DOT || OP == BLAS_DOT2) {
+            R v0[24];
             load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
-            R d = 0;
+            {
+                R v1[24];
+                load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+                R d = 0;
 #pragma unroll
-            for (int r = 0; r < 24; r++) d += v0[r] * v1[r];
-            p0 = (double)d;
-            if (op == BLAS_DOT2) {
+                for (int r = 0; r < 24; r++) d += v0[r] * v1[r];
+                p0 = (double)d;
+            }
+            if constexpr (OP == BLAS_DOT2) {
+                R v2[24];
                 load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
                 R e = 0;
 #pragma unroll
                 for (int r = 0; r < 24; r++) e += v0[r] * v2[r];
                 p1 = (double)e;
             }
-        } break;
-        case BLAS_NORM2: {
+        } else if constexpr (OP == BLAS_NORM2) {
+            R v0[24];
             load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
             R d = 0;
 #pragma unroll
             for (int r = 0; r < 24; r++) d += v0[r] * v0[r];
             p0 = (double)d;
-        } break;
-        case BLAS_CG_UPDATE: {
-            // x += alpha p ; r -= alpha Ap ; |r|^2
+        } else if constexpr (OP == BLAS_CG_UPDATE) {
+            // x += alpha p ; r -= alpha Ap ; |r|^2 (the two halves in turn)
             const R al = (R)(a.scal[0][seg] * a.scal_sign[0]);
-            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
-            load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
-            load_any<R>(a.p[3], a.v[3], n, i, s, Ls, v3);
-            R d = 0;
+            {
+                R v0[24], v1[24];
+                load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+                load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
 #pragma unroll
-            for (int r = 0; r < 24; r++) {
-                v0[r] += al * v1[r];
-                v2[r] -= al * v3[r];
-                d += v2[r] * v2[r];
+                for (int r = 0; r < 24; r++) v0[r] += al * v1[r];
+                store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
             }
-            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-            store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
-            p0 = (double)d;
-        } break;
-        case BLAS_XPAY: {
+            {
+                R v2[24], v3[24];
+                load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                load_any<R>(a.p[3], a.v[3], n, i, s, Ls, v3);
+                R d = 0;
+#pragma unroll
+                for (int r = 0; r < 24; r++) {
+                    v2[r] -= al * v3[r];
+                    d += v2[r] * v2[r];
+                }
+                store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                p0 = (double)d;
+            }
+        } else if constexpr (OP == BLAS_XPAY) {
             // v0 = v1 + beta v0
             const R be = (R)(a.scal[0][seg] * a.scal_sign[0]);
+            R v0[24], v1[24];
             load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
             load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
 #pragma unroll
             for (int r = 0; r < 24; r++) v0[r] = v1[r] + be * v0[r];
             store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-        } break;
-        case BLAS_AXPY_ZERO: {
+        } else if constexpr (OP == BLAS_AXPY_ZERO) {
+            R v0[24];
 #pragma unroll
             for (int r = 0; r < 24; r++) v0[r] = 0;
             store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-        } break;
-        case BLAS_COPY: {
+        } else if constexpr (OP == BLAS_COPY) {
+            R v1[24];
             load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
             store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v1);
             if (a.v[2]) store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v1);
@@ -196,52 +206,71 @@ __global__ void __launch_bounds__(512) blas_kernel(BlasOp op, BlasArgs a)
 #pragma unroll
             for (int r = 0; r < 24; r++) d += v1[r] * v1[r];
             p0 = (double)d;
-        } break;
-        case BLAS_RESIDUAL: {
-            // v0 = v1 - v2 ; optional copy into v3 ; |v0|^2 ; optional v4 (x += xacc; xacc = 0)
+        } else if constexpr (OP == BLAS_RESIDUAL) {
+            // v0 = v1 - v2 ; optional copy into v3 ; |v0|^2
+            R v1[24];
             load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
-            load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+            {
+                R v2[24];
+                load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+#pragma unroll
+                for (int r = 0; r < 24; r++) v1[r] -= v2[r];
+            }
             R d = 0;
 #pragma unroll
-            for (int r = 0; r < 24; r++) {
-                v0[r] = v1[r] - v2[r];
-                d += v0[r] * v0[r];
-            }
-            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-            if (a.v[3]) store_any<R>(a.p[3], a.v[3], n, i, s, Ls, v0);
+            for (int r = 0; r < 24; r++) d += v1[r] * v1[r];
+            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v1);
+            if (a.v[3]) store_any<R>(a.p[3], a.v[3], n, i, s, Ls, v1);
             p0 = (double)d;
-        } break;
         }
     }
-    if (a.mphi_out) {
-        // u = M_phi v for the vector just written: the CTA holds whole Ls
-        // columns, so psi_{s+-1} of the same site come from shared memory.
-        // (M_phi v)_s = -(b v_s + c (P_- v_{s+1} + P_+ v_{s-1}))/2, wraps times -mass.
-        extern __shared__ __align__(16) unsigned char blas_smem[];
-        R *sv = reinterpret_cast<R *>(blas_smem);
-        R v[24];
-        if (active) load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v);
-        if (active) {
+    if constexpr (OP == BLAS_COPY || OP == BLAS_XPAY) {
+        if (a.mphi_out) {
+            // u = M_phi v for the vector just written (as stored): the CTA holds
+            // whole Ls columns, so psi_{s+-1} of the same site come from shared
+            // memory.  (M_phi v)_s = -(b v_s + c (P_- v_{s+1} + P_+ v_{s-1}))/2,
+            // wrap terms times -mass.
+            extern __shared__ __align__(16) unsigned char blas_smem[];
+            R *sv = reinterpret_cast<R *>(blas_smem);
+            R v[24];
+            if (active) {
+                load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v);
 #pragma unroll
-            for (int r = 0; r < 24; r++) sv[(jl * Ls + s) * 24 + r] = v[r];
-        }
-        __syncthreads();
-        if (active) {
-            const int sys = a.tile_sys ? a.tile_sys[i / kSegPad] : 0;
-            const double *mp = a.mphi + 5 * sys;
-            const R cb = (R)(-0.5 * mp[0]), cc = (R)(-0.5 * mp[1]), wm = (R)(-mp[2]);
-            const int sp = s + 1 < Ls ? s + 1 : 0, sm = s > 0 ? s - 1 : Ls - 1;
-            const R fp = s + 1 < Ls ? cc : cc * wm, fm = s > 0 ? cc : cc * wm;
-            const R *vp = sv + (jl * Ls + sp) * 24, *vm = sv + (jl * Ls + sm) * 24;
-            R u[24];
+                for (int r = 0; r < 24; r++) sv[(jl * Ls + s) * 24 + r] = v[r];
+            }
+            __syncthreads();
+            if (active) {
+                const int sys = a.tile_sys ? a.tile_sys[i / kSegPad] : 0;
+                const double *mp = a.mphi + 5 * sys;
+                const R cb = (R)(-0.5 * mp[0]), cc = (R)(-0.5 * mp[1]), wm = (R)(-mp[2]);
+                const int sp = s + 1 < Ls ? s + 1 : 0, sm = s > 0 ? s - 1 : Ls - 1;
+                const R fp = s + 1 < Ls ? cc : cc * wm, fm = s > 0 ? cc : cc * wm;
+                const R *vp = sv + (jl * Ls + sp) * 24, *vm = sv + (jl * Ls + sm) * 24;
+                R u[24];
 #pragma unroll
-            for (int r = 0; r < 12; r++) u[r] = cb * v[r] + fp * vp[r];
+                for (int r = 0; r < 12; r++) u[r] = cb * v[r] + fp * vp[r];
 #pragma unroll
-            for (int r = 12; r < 24; r++) u[r] = cb * v[r] + fm * vm[r];
-            store_any<R>(a.mphi_prec, a.mphi_out, n, i, s, Ls, u);
+                for (int r = 12; r < 24; r++) u[r] = cb * v[r] + fm * vm[r];
+                store_any<R>(a.mphi_prec, a.mphi_out, n, i, s, Ls, u);
+            }
         }
     }
-    if (a.part) block_reduce_store(p0, p1, op == BLAS_DOT2 ? 2 : 1, a.part, cta);
+    if (a.part) block_reduce_store(p0, p1, ncomp, a.part, cta);
+}
+
+template <typename R>
+static void launch_blas_t(BlasOp op, const BlasArgs &a, unsigned nblk, int nthr, size_t sm, cudaStream_t st)
+{
+    switch (op) {
+    case BLAS_DOT: blas_kernel<R, BLAS_DOT><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_NORM2: blas_kernel<R, BLAS_NORM2><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_CG_UPDATE: blas_kernel<R, BLAS_CG_UPDATE><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_XPAY: blas_kernel<R, BLAS_XPAY><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_AXPY_ZERO: blas_kernel<R, BLAS_AXPY_ZERO><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_COPY: blas_kernel<R, BLAS_COPY><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_DOT2: blas_kernel<R, BLAS_DOT2><<<nblk, nthr, sm, st>>>(a); break;
+    case BLAS_RESIDUAL: blas_kernel<R, BLAS_RESIDUAL><<<nblk, nthr, sm, st>>>(a); break;
+    }
 }
 
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
@@ -254,8 +283,8 @@ void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
     const long end = a.site_end ? a.site_end : a.nsite;
     const unsigned nblk = (unsigned)((end - a.site0 + a.tile - 1) / a.tile);
     const size_t sm = a.mphi_out ? (size_t)nthr * 24 * (dbl ? 8 : 4) : 0;
-    if (dbl) blas_kernel<double><<<nblk, nthr, sm, st>>>(op, a);
-    else blas_kernel<float><<<nblk, nthr, sm, st>>>(op, a);
+    if (dbl) launch_blas_t<double>(op, a, nblk, nthr, sm, st);
+    else launch_blas_t<float>(op, a, nblk, nthr, sm, st);
     DWF_CUDA(cudaGetLastError());
     count_launch();
 }
