@@ -14,12 +14,15 @@ void count_launch(long long n) { g_launches += n; }
 long long launch_count() { return g_launches.load(); }
 
 // ------------------------------------------------ precision-generic access
+// A single-precision kernel never sees FP64 operands (launch_blas sends those
+// to the double instance), so its FP64 branches are compiled out.
 template <typename R>
 __device__ __forceinline__ void load_any(Prec p, const void *base, long nsite, long site, int s,
                                          int Ls, R *v)
 {
     switch (p) {
     case P64: {
+        if constexpr (sizeof(R) == 4) break;
         double t[24];
         load_sp<TF64>(base, nsite, site, s, Ls, t);
 #pragma unroll
@@ -51,6 +54,7 @@ __device__ __forceinline__ void store_any(Prec p, void *base, long nsite, long s
 {
     switch (p) {
     case P64: {
+        if constexpr (sizeof(R) == 4) break;
         double t[24];
 #pragma unroll
         for (int r = 0; r < 24; r++) t[r] = (double)v[r];
@@ -164,13 +168,19 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
             const R al = (R)(a.scal[0][seg] * a.scal_sign[0]);
             {
                 R v0[24], v1[24];
-                load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+                if (a.x_zero) {
+#pragma unroll
+                    for (int r = 0; r < 24; r++) v0[r] = 0;
+                } else {
+                    load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+                }
                 load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
 #pragma unroll
                 for (int r = 0; r < 24; r++) v0[r] += al * v1[r];
-                store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+                if (a.v[4]) store_any<R>(a.p[4], a.v[4], n, i, s, Ls, v0);
+                else store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
             }
-            {
+            if (a.v[2]) {
                 R v2[24], v3[24];
                 load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
                 load_any<R>(a.p[3], a.v[3], n, i, s, Ls, v3);

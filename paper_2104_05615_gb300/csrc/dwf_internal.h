@@ -132,6 +132,10 @@ struct BlasArgs {
     void *mphi_out;
     Prec mphi_prec;
     const double *mphi;
+    // BLAS_CG_UPDATE: x_zero = x is zero on input (not read); v[4] (if set)
+    // receives the updated x in precision p[4] instead of v[0]; v[2] null:
+    // only the x half (no r update, no partial)
+    int x_zero;
 };
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st);
 

@@ -163,14 +163,12 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             t.s0 = rr;
             launch_scalar(SC_SUM, t, c.st);
         }
-        {
-            BlasArgs a = blas(E, n, L, nullptr, nullptr);
-            range(a);
-            a.v[0] = zin;
-            a.p[0] = P32;
-            launch_blas(BLAS_AXPY_ZERO, a, c.st);
-        }
+        // z starts at zero: the first update writes alpha p without reading z;
+        // the last one writes z in the outer precision straight into the
+        // result (FP32 outer, full Ls) and skips the r half
+        const bool z_direct = !red && po == P32;
         for (int it = 0; it < P.inner_iters; it++) {
+            const bool last = it + 1 == P.inner_iters;
             E.timed_begin(1 + it);
             const int tile = E.apply_local(pi, L, Apin, pin, c.part, b0, b1, uin);
             E.timed_end(1 + it);
@@ -179,15 +177,20 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             t.s0 = rr;
             t.s1 = al;
             launch_scalar(SC_ALPHA, t, c.st);
-            BlasArgs a = blas(E, n, L, tsb, c.part);
+            BlasArgs a = blas(E, n, L, tsb, (last && z_direct) ? nullptr : c.part);
             range(a);
             a.v[0] = zin; a.p[0] = P32;
             a.v[1] = pin; a.p[1] = pi;
             a.v[2] = rin; a.p[2] = pi;
             a.v[3] = Apin; a.p[3] = pi;
             a.scal[0] = al;
+            a.x_zero = it == 0;
+            if (last && z_direct) {
+                a.v[4] = z; a.p[4] = po;
+                a.v[2] = a.v[3] = nullptr;
+            }
             launch_blas(BLAS_CG_UPDATE, a, c.st);
-            if (it + 1 < P.inner_iters) {
+            if (!last) {
                 ScalarArgs u = scal(E.seg_blk, c.part, 1, kBlasTile);
                 segs(u);
                 u.s0 = rr;
@@ -211,9 +214,9 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
         a.v[0] = z;
         a.p[0] = po;
         launch_blas(BLAS_AXPY_ZERO, a, c.st);
-    } else {
+    } else if (po != P32) {
         launch_convert(po, z, P32, zin, n, E.Ls, c.st);
-    }
+    }  // else the last inner update wrote z
 }
 
 // r64 = b64 - A x64 ; r = r64 (in po) ; rr (per system) on the device
