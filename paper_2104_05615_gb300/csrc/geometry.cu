@@ -120,6 +120,37 @@ bool build_geometry(LatticeGeom &g, const int dims[4], const int subd[4], int an
             return dist(a.data()) == 0;
         });
     }
+    // Halo sites have only some of their eight neighbours in the input region
+    // of the stage that writes them (stage 1 for O1: the interior; stage 2 for
+    // E2: O1).  Ordering each halo by that neighbour pattern keeps the sites
+    // of a warp on the same directions (no divergence in the hop).
+    {
+        auto pattern = [&](const std::array<int, 4> &a, int maxd) {
+            int m = 0;
+            for (int mu = 0; mu < 4; mu++)
+                for (int d = 0; d < 2; d++) {
+                    int n[4] = {a[0], a[1], a[2], a[3]};
+                    n[mu] += d ? -1 : 1;
+                    if (!part[mu]) n[mu] = (n[mu] + g.sub[mu]) % g.sub[mu];
+                    if (dist(n) <= maxd) m |= 1 << (2 * mu + d);
+                }
+            return m;
+        };
+        auto by_pattern = [&](std::vector<std::array<int, 4>>::iterator b,
+                              std::vector<std::array<int, 4>>::iterator e, int maxd) {
+            std::vector<std::pair<int, std::array<int, 4>>> tmp;
+            for (auto it = b; it != e; ++it) tmp.push_back({pattern(*it, maxd), *it});
+            std::stable_sort(tmp.begin(), tmp.end(),
+                             [](const auto &x, const auto &y) { return x.first < y.first; });
+            for (auto &t : tmp) *b++ = t.second;
+        };
+        auto ob = std::find_if(o1.begin(), o1.end(),
+                               [&](const std::array<int, 4> &a) { return dist(a.data()) != 0; });
+        by_pattern(ob, o1.end(), 0);
+        e2_halo1.insert(e2_halo1.end(), e2_halo2.begin(), e2_halo2.end());
+        e2_halo2.clear();
+        by_pattern(e2_halo1.begin(), e2_halo1.end(), 1);
+    }
     if ((int)interior.size() != g.Nb) {
         err = "internal: interior count mismatch";
         return false;
