@@ -385,7 +385,7 @@ def main():
                          "and time to solution against the inner iteration count and precision")
     ap.add_argument("--op-reps", type=int, default=3)
     ap.add_argument("--kcfg", default=None,
-                    help="fixed stage launch config 'tile,gather' for both operators (ops mode)")
+                    help="fixed stage launch config 'tile,gather' for both operators (ops and solve modes)")
     ap.add_argument("--ref-iters", type=int, default=300,
                     help="outer iterations the oracle arm extrapolates to")
     args = ap.parse_args()
@@ -513,6 +513,13 @@ def main():
         # launches a profiler should skip
         p = solver_params(cfg, cfg["solver"] == "mspcg")
         p.maxiter = 2
+        if args.kcfg:
+            # profilers distort the autotuner's timings: fix the shape it picks
+            from paper_2104_05615_gb300.lattice import PREC
+            tile, gather = (int(v) for v in args.kcfg.split(","))
+            if cfg["solver"] == "mspcg":
+                B.dwf_set_kernel_config(lat.h, PREC[cfg.get("inner_prec", "f16")], 1, tile, gather)
+            B.dwf_set_kernel_config(lat.h, PREC[cfg.get("outer_prec", "f32")], 0, tile, gather)
         x = torch.zeros_like(bd)
         fn = B.dwf_mspcg if cfg["solver"] == "mspcg" else B.dwf_cg
         fn(lat.h, x, bd, p, raise_on_noconv=False)
@@ -532,6 +539,13 @@ def main():
     # --- MSPCG time to solution (the headline)
     mspcg = cfg["solver"] == "mspcg"
     params = solver_params(cfg, mspcg)
+    if args.kcfg:
+        # fixed stage launch shape instead of the autotuner's choice
+        from paper_2104_05615_gb300.lattice import PREC
+        tile, gather = (int(v) for v in args.kcfg.split(","))
+        if mspcg:
+            B.dwf_set_kernel_config(lat.h, PREC[cfg.get("inner_prec", "f16")], 1, tile, gather)
+        B.dwf_set_kernel_config(lat.h, PREC[cfg.get("outer_prec", "f32")], 0, tile, gather)
     with ClockSampler(local_rank) as clk:
         times, st, x, launches = time_solves(lat, bd, params, mspcg, K, W, flush, barrier)
     t_step = maxall(statistics.mean(times))
