@@ -380,12 +380,19 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves", "inner"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves", "inner", "train"],
                     help="ops: only apply the operators (for profilers); inner: outer iterations "
                          "and time to solution against the inner iteration count and precision")
     ap.add_argument("--op-reps", type=int, default=3)
     ap.add_argument("--kcfg", default=None,
                     help="fixed stage launch config 'tile,gather' for both operators (ops and solve modes)")
+    ap.add_argument("--train-steps", type=int, default=8, help="train mode: descent steps")
+    ap.add_argument("--train-mus", default=None,
+                    help="train mode: comma-separated suppression factors mu (default: the workload's)")
+    ap.add_argument("--train-residual-iters", default="50,100,200",
+                    help="train mode: outer iterations after which the residuals v_i are taken")
+    ap.add_argument("--train-inverse-iters", type=int, default=40,
+                    help="train mode: inner CG iterations standing in for Mhat^-1")
     ap.add_argument("--ref-iters", type=int, default=300,
                     help="outer iterations the oracle arm extrapolates to")
     args = ap.parse_args()
@@ -427,6 +434,56 @@ def main():
         tg = time_op(lat, B.DWF_OP_DDAGD, "f32", args.op_reps, flush)
         if rank == 0:
             print(json.dumps({"local_ms": tl * 1e3, "global_ms": tg * 1e3}))
+        return
+    if args.mode == "train":
+        # Sec. 3.3: train the reduced-Ls transform T on residuals of the solve
+        # with the original operators, then solve with the heuristic and the
+        # trained T (MSPCG + reduced Ls) and compare
+        from paper_2104_05615_gb300.lattice import heuristic_T
+        from paper_2104_05615_gb300.reduced_ls import DeviceBackend, TransformTrainer
+        if not cfg.get("Ls_hat"):
+            raise SystemExit("train mode needs a reduced-Ls workload (--config C4)")
+        Ls, Lh = cfg["Ls"], cfg["Ls_hat"]
+        mus = [float(m) for m in args.train_mus.split(",")] if args.train_mus else [cfg["mu"]]
+        vs = []
+        t0 = time.perf_counter()
+        for it in (int(k) for k in args.train_residual_iters.split(",")):
+            p = solver_params(cfg, True)
+            p.use_reduced_ls = 0
+            p.maxiter = it
+            x = torch.zeros_like(bd)
+            B.dwf_mspcg(lat.h, x, bd, p, raise_on_noconv=False)
+            r = bd - lat.apply("DdagD", x, "f64")
+            vs.append(r / torch.linalg.vector_norm(r))
+        t_vs = time.perf_counter() - t0
+        T0 = heuristic_T(Ls, Lh)
+        for mu in mus:
+            tr = TransformTrainer(DeviceBackend(lat, Lh, inverse_iters=args.train_inverse_iters), vs, mu)
+            log = (lambda k, c, e, pr: print(json.dumps({"mu": mu, "step": k, "chi2_rel": c, "eta": e,
+                                                          "chi2_rel_after": pr}), flush=True)) if rank == 0 else None
+            t0 = time.perf_counter()
+            T, hist = tr.train(T0, steps=args.train_steps, log=log)
+            t_train = time.perf_counter() - t0
+            rows = []
+            for name, Tm in (("heuristic", T0), ("trained", T)):
+                lat.set_reduced_ls(Lh, Tm, mu)
+                p = solver_params(cfg, True)
+                x = torch.zeros_like(bd)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = B.dwf_mspcg(lat.h, x, bd, p, raise_on_noconv=False)
+                e1.record()
+                e1.synchronize()
+                rows.append({"T": name, "outer_iters": st.outer_iters, "inner_iters_total": st.inner_iters_total,
+                             "seconds": e0.elapsed_time(e1) / 1000.0, "true_residual": st.true_residual,
+                             "converged": bool(st.converged)})
+            if rank == 0:
+                print(json.dumps({"mode": "train", "workload": cfg_name, "Ls": Ls, "Ls_hat": Lh, "mu": mu,
+                                  "residual_iters": args.train_residual_iters, "residual_seconds": t_vs,
+                                  "train_steps": args.train_steps, "inverse_iters": args.train_inverse_iters,
+                                  "train_seconds": t_train, "chi2_rel_history": hist, "solves": rows}),
+                      flush=True)
         return
     if args.mode == "inner":
         # Table 1's trend on this workload: plain CG, then MSPCG with k inner

@@ -180,6 +180,38 @@ dwf_status dwf_precondition(dwf_handle *h, double *z_dev, const double *r_dev,
  * row index s*4 + spin, column index t*4 + spin; trivial in colour. */
 dwf_status dwf_set_reduced_ls(dwf_handle *h, int Ls_hat, const double *T_host, double mu);
 
+/* Training the reduced-Ls transform T (Sec. 3.3).  The loss
+ *   chi^2(T) = sum_i | M (T^+ Mhat^-1 T + mu) v_i - v_i |^2
+ * (M the local operator (+)_s A_s at Ls, Mhat the one at Ls_hat) and its
+ * gradient are assembled from the three calls below plus dwf_apply with
+ * DWF_OP_LOCAL_DDAGD; all fields are canonical even-checkerboard FP64 device
+ * arrays of this handle's lattice (Ls or Ls_hat slices as stated).
+ *
+ * dwf_reduced_local_inverse: out = CG_iters(Mhat) in, x0 = 0, every block
+ * independently (the inner solve of the preconditioner run to `iters`
+ * iterations, standing in for Mhat^-1); p->inner_prec (FP32, FP16 or BF16;
+ * the 16-bit formats need Ls_hat <= 16) sets the inner storage, p null means
+ * dwf_default_params.  in, out: Ls_hat slices, out != in.
+ *
+ * dwf_apply_T: dagger = 0: out (Ls_hat slices) = T in (Ls slices);
+ * dagger = 1: out (Ls slices) = T^+ in (Ls_hat slices).  T_host: (4 Ls_hat) x
+ * (4 Ls) complex as double pairs, row s*4 + spin, column t*4 + spin, trivial in
+ * colour (the layout of dwf_set_reduced_ls); applied in single precision.
+ *
+ * dwf_T_contract: G_host ((4 La) x (4 Lb) complex, double pairs, row-major) =
+ * sum over sites x and colours c of a[s][x][spin][c] conj(b[t][x][spin'][c]),
+ * row s*4 + spin, column t*4 + spin'; a has La slices, b has Lb slices,
+ * 16 La Lb <= 4096.  Summed in FP64 in a fixed order (deterministic).
+ *
+ * All three synchronise the handle's stream before returning; DWF_EINVAL for
+ * bad arguments, DWF_ECUDA / DWF_ENOMEM on device failures. */
+dwf_status dwf_reduced_local_inverse(dwf_handle *h, double *out_dev, const double *in_dev, int Ls_hat,
+                                     int iters, const dwf_solver_params *p);
+dwf_status dwf_apply_T(dwf_handle *h, double *out_dev, const double *in_dev, const double *T_host,
+                       int Ls_hat, int dagger);
+dwf_status dwf_T_contract(dwf_handle *h, double *G_host, const double *a_dev, int La, const double *b_dev,
+                          int Lb);
+
 /* Ablation of the snake terms (Sec. 2.3, Eq. (eq:diri)): with on != 0 every
  * later use of the local operator A_s on this handle (dwf_apply with
  * DWF_OP_LOCAL_DDAGD, dwf_precondition, dwf_mspcg) applies Dirichlet walls at

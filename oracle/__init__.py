@@ -228,6 +228,54 @@ class Oracle:
 
         return Pe * Dt_dag(Dt(Pe * x))
 
+    def reduced_local_inverse(self, r_hat, sub, Ls_hat, tol=1e-13, maxiter=5000):
+        """Mhat^-1 r_hat for Mhat = (+)_s A_s at the reduced extent Ls_hat (same
+        b, c, M5, mass): plain CG to a relative residual tol, i.e. the exact
+        inverse the transform training of Sec. 3.3 differentiates through."""
+        o = self.with_Ls(Ls_hat)
+        b = _c(r_hat).reshape(o.cb_shape())
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr = np.vdot(r, r).real
+        bb = rr
+        for _ in range(maxiter):
+            if rr <= tol * tol * bb:
+                break
+            Ap = o.local_DdagD(p, sub)
+            al = rr / np.vdot(p, Ap).real
+            x += al * p
+            r -= al * Ap
+            rr_new = np.vdot(r, r).real
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+        return x
+
+    @staticmethod
+    def outer_contract(a, b):
+        """sum over sites and colours of a b^+: rows s*4 + spin of a (La slices),
+        columns t*4 + spin of b (Lb slices)."""
+        La, Lb = a.shape[0], b.shape[0]
+        return np.einsum("sxmc,txnc->smtn", a, np.conj(b)).reshape(4 * La, 4 * Lb)
+
+    def T_loss(self, T, mu, vs, sub, Ls_hat, grad=True):
+        """Sec. 3.3: chi^2(T) = sum_i |M (T^+ Mhat^-1 T + mu) v_i - v_i|^2, M the
+        local operator (+)_s A_s at Ls, Mhat the one at Ls_hat.  With
+        w = Mhat^-1 T v, e = M (T^+ w + mu v) - v, g = M e, u = Mhat^-1 T g,
+        d chi^2 = 2 Re <G, dT>_F with G = sum_i (w_i g_i^+ + u_i v_i^+) (outer
+        products contracted over sites and colours).  Returns (chi^2, G)."""
+        chi2, G = 0.0, np.zeros_like(np.asarray(T, dtype=np.complex128))
+        for v in vs:
+            v = _c(v).reshape(self.cb_shape())
+            w = self.reduced_local_inverse(self.T_apply(T, v, Ls_hat), sub, Ls_hat)
+            e = self.local_DdagD(self.T_apply(T, w, Ls_hat, dagger=True) + mu * v, sub) - v
+            chi2 += np.vdot(e, e).real
+            if grad:
+                g = self.local_DdagD(e, sub)
+                u = self.reduced_local_inverse(self.T_apply(T, g, Ls_hat), sub, Ls_hat)
+                G += self.outer_contract(w, g) + self.outer_contract(u, v)
+        return chi2, G
+
     def T_apply(self, T, x, Ls_hat, dagger=False):
         x = _c(x)
         nsite = x.shape[1]

@@ -82,6 +82,9 @@ def lib() -> C.CDLL:
             "dwf_precondition": (i, [vp, vp, vp, C.POINTER(dwf_solver_params)]),
             "dwf_set_reduced_ls": (i, [vp, i, vp, d]),
             "dwf_set_local_truncated": (i, [vp, i]),
+            "dwf_reduced_local_inverse": (i, [vp, vp, vp, i, i, C.POINTER(dwf_solver_params)]),
+            "dwf_apply_T": (i, [vp, vp, vp, vp, i, i]),
+            "dwf_T_contract": (i, [vp, vp, vp, i, vp, i]),
             "dwf_batch_create": (i, [C.POINTER(vp), C.POINTER(vp), i]),
             "dwf_batch_destroy": (None, [vp]),
             "dwf_batch_mspcg": (i, [vp, C.POINTER(vp), C.POINTER(vp),
@@ -236,6 +239,28 @@ def dwf_set_reduced_ls(h, Ls_hat, T_host, mu):
 
 def dwf_set_local_truncated(h, on):
     return check(lib().dwf_set_local_truncated(h, int(bool(on))), h)
+
+
+def dwf_reduced_local_inverse(h, out, inp, Ls_hat, iters, params=None):
+    """out = CG_iters(Mhat) inp on canonical FP64 device tensors (Ls_hat slices)."""
+    p = params if params is not None else default_params()
+    return check(lib().dwf_reduced_local_inverse(h, _ptr(out), _ptr(inp), int(Ls_hat), int(iters),
+                                                 C.byref(p)), h)
+
+
+def dwf_apply_T(h, out, inp, T_host, Ls_hat, dagger=False):
+    """out = T inp (dagger False) or T^+ inp on canonical FP64 device tensors."""
+    import numpy as np
+    T = np.ascontiguousarray(T_host, dtype=np.complex128)
+    return check(lib().dwf_apply_T(h, _ptr(out), _ptr(inp), _ptr(T), int(Ls_hat), int(bool(dagger))), h)
+
+
+def dwf_T_contract(h, a, La, b, Lb):
+    """sum over sites and colours of a b^+ as a (4 La) x (4 Lb) complex numpy matrix."""
+    import numpy as np
+    G = np.empty((4 * La, 4 * Lb), dtype=np.complex128)
+    check(lib().dwf_T_contract(h, _ptr(G), _ptr(a), int(La), _ptr(b), int(Lb)), h)
+    return G
 
 
 def dwf_batch_create(handles):

@@ -320,6 +320,66 @@ dwf_status dwf_set_reduced_ls(dwf_handle *h, int Ls_hat, const double *T_host, d
     });
 }
 
+dwf_status dwf_reduced_local_inverse(dwf_handle *h, double *out, const double *in, int Ls_hat, int iters,
+                                     const dwf_solver_params *p)
+{
+    if (!h || !out || !in || out == in || Ls_hat < 1 || Ls_hat > 32 || iters < 0) return DWF_EINVAL;
+    dwf_solver_params P;
+    if (p) P = *p;
+    else dwf_default_params(&P);
+    if (!prec_ok(P.inner_prec) || P.inner_prec == DWF_F64) return DWF_EINVAL;
+    if ((P.inner_prec == DWF_F16 || P.inner_prec == DWF_BF16) && Ls_hat > 16) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        reduced_local_inverse(*h->E, out, in, Ls_hat, iters, P);
+        DWF_CUDA(cudaStreamSynchronize(h->E->st));
+        if (h->E->check_err()) {
+            h->err = "a bounded device wait gave up";
+            return DWF_ETIMEOUT;
+        }
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_apply_T(dwf_handle *h, double *out, const double *in, const double *T_host, int Ls_hat,
+                       int dagger)
+{
+    if (!h || !out || !in || !T_host || out == in || Ls_hat < 1 || Ls_hat > 32) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        Engine &E = *h->E;
+        const int Ls = h->Ls;
+        const long n = E.ne;
+        const size_t nT = (size_t)4 * Ls_hat * 4 * Ls * 2;
+        std::vector<float> Tf(T_host, T_host + nT);
+        float *Td = (float *)E.ws("T_apply_matrix", nT * sizeof(float));
+        DWF_CUDA(cudaMemcpyAsync(Td, Tf.data(), nT * sizeof(float), cudaMemcpyHostToDevice, E.st));
+        const int Lin = dagger ? Ls_hat : Ls, Lout = dagger ? Ls : Ls_hat;
+        void *pin = E.ws("T_apply_in", field_bytes(P64, n, Lin));
+        void *pout = E.ws("T_apply_out", field_bytes(P64, n, Lout));
+        const LatticeGeom &g = *E.sys[0].g;
+        launch_pack(P64, pin, in, E.perm[0], g.ne(), g.Vh, Lin, E.st);
+        launch_tapply(P64, pout, Lout, P64, pin, Lin, Td, n, dagger ? 1 : 0, nullptr, P64, 0.0, E.st);
+        launch_unpack(P64, out, pout, E.perm[0], g.ne(), g.Vh, Lout, E.st);
+        DWF_CUDA(cudaStreamSynchronize(E.st));
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_T_contract(dwf_handle *h, double *G_host, const double *a, int La, const double *b, int Lb)
+{
+    if (!h || !G_host || !a || !b || La < 1 || Lb < 1 || 16 * La * Lb > 4096) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        Engine &E = *h->E;
+        const size_t nG = (size_t)16 * La * Lb * 2;
+        double *Gd = (double *)E.ws("T_contract_G", nG * sizeof(double));
+        void *work = E.ws("T_contract_work", tcontract_workspace_bytes(La, Lb));
+        const LatticeGeom &g = *E.sys[0].g;
+        launch_tcontract(Gd, a, La, b, Lb, g.Vh, work, E.st);
+        DWF_CUDA(cudaMemcpyAsync(G_host, Gd, nG * sizeof(double), cudaMemcpyDeviceToHost, E.st));
+        DWF_CUDA(cudaStreamSynchronize(E.st));
+        return DWF_OK;
+    });
+}
+
 dwf_status dwf_set_local_truncated(dwf_handle *h, int on)
 {
     if (!h) return DWF_EINVAL;

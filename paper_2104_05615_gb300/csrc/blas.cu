@@ -4,6 +4,7 @@
 // the per-segment scalar recurrences of CG, and the reduced-Ls transform
 // z = T^+ zhat + mu r of Sec. 3.3.
 #include <atomic>
+#include <stdexcept>
 
 #include "device_common.cuh"
 
@@ -14,15 +15,15 @@ void count_launch(long long n) { g_launches += n; }
 long long launch_count() { return g_launches.load(); }
 
 // ------------------------------------------------ precision-generic access
-// A single-precision kernel never sees FP64 operands (launch_blas sends those
-// to the double instance), so its FP64 branches are compiled out.
-template <typename R>
+// kNo64: the caller never passes FP64 operands (blas_kernel<float>: launch_blas
+// sends those to the double instance), so the FP64 branches are compiled out.
+template <typename R, bool kNo64 = false>
 __device__ __forceinline__ void load_any(Prec p, const void *base, long nsite, long site, int s,
                                          int Ls, R *v)
 {
     switch (p) {
     case P64: {
-        if constexpr (sizeof(R) == 4) break;
+        if constexpr (kNo64) break;
         double t[24];
         load_sp<TF64>(base, nsite, site, s, Ls, t);
 #pragma unroll
@@ -48,13 +49,13 @@ __device__ __forceinline__ void load_any(Prec p, const void *base, long nsite, l
     } break;
     }
 }
-template <typename R>
+template <typename R, bool kNo64 = false>
 __device__ __forceinline__ void store_any(Prec p, void *base, long nsite, long site, int s,
                                           int Ls, const R *v)
 {
     switch (p) {
     case P64: {
-        if constexpr (sizeof(R) == 4) break;
+        if constexpr (kNo64) break;
         double t[24];
 #pragma unroll
         for (int r = 0; r < 24; r++) t[r] = (double)v[r];
@@ -139,10 +140,10 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
     if (active) {
         if constexpr (OP == BLAS_DOT || OP == BLAS_DOT2) {
             R v0[24];
-            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            load_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
             {
                 R v1[24];
-                load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+                load_any<R, sizeof(R) == 4>(a.p[1], a.v[1], n, i, s, Ls, v1);
                 R d = 0;
 #pragma unroll
                 for (int r = 0; r < 24; r++) d += v0[r] * v1[r];
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
             }
             if constexpr (OP == BLAS_DOT2) {
                 R v2[24];
-                load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                load_any<R, sizeof(R) == 4>(a.p[2], a.v[2], n, i, s, Ls, v2);
                 R e = 0;
 #pragma unroll
                 for (int r = 0; r < 24; r++) e += v0[r] * v2[r];
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
             }
         } else if constexpr (OP == BLAS_NORM2) {
             R v0[24];
-            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            load_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
             R d = 0;
 #pragma unroll
             for (int r = 0; r < 24; r++) d += v0[r] * v0[r];
@@ -172,46 +173,46 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
 #pragma unroll
                     for (int r = 0; r < 24; r++) v0[r] = 0;
                 } else {
-                    load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+                    load_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
                 }
-                load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+                load_any<R, sizeof(R) == 4>(a.p[1], a.v[1], n, i, s, Ls, v1);
 #pragma unroll
                 for (int r = 0; r < 24; r++) v0[r] += al * v1[r];
-                if (a.v[4]) store_any<R>(a.p[4], a.v[4], n, i, s, Ls, v0);
-                else store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+                if (a.v[4]) store_any<R, sizeof(R) == 4>(a.p[4], a.v[4], n, i, s, Ls, v0);
+                else store_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
             }
             if (a.v[2]) {
                 R v2[24], v3[24];
-                load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
-                load_any<R>(a.p[3], a.v[3], n, i, s, Ls, v3);
+                load_any<R, sizeof(R) == 4>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                load_any<R, sizeof(R) == 4>(a.p[3], a.v[3], n, i, s, Ls, v3);
                 R d = 0;
 #pragma unroll
                 for (int r = 0; r < 24; r++) {
                     v2[r] -= al * v3[r];
                     d += v2[r] * v2[r];
                 }
-                store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                store_any<R, sizeof(R) == 4>(a.p[2], a.v[2], n, i, s, Ls, v2);
                 p0 = (double)d;
             }
         } else if constexpr (OP == BLAS_XPAY) {
             // v0 = v1 + beta v0
             const R be = (R)(a.scal[0][seg] * a.scal_sign[0]);
             R v0[24], v1[24];
-            load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
-            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            load_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            load_any<R, sizeof(R) == 4>(a.p[1], a.v[1], n, i, s, Ls, v1);
 #pragma unroll
             for (int r = 0; r < 24; r++) v0[r] = v1[r] + be * v0[r];
-            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            store_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
         } else if constexpr (OP == BLAS_AXPY_ZERO) {
             R v0[24];
 #pragma unroll
             for (int r = 0; r < 24; r++) v0[r] = 0;
-            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v0);
+            store_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v0);
         } else if constexpr (OP == BLAS_COPY) {
             R v1[24];
-            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
-            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v1);
-            if (a.v[2]) store_any<R>(a.p[2], a.v[2], n, i, s, Ls, v1);
+            load_any<R, sizeof(R) == 4>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            store_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v1);
+            if (a.v[2]) store_any<R, sizeof(R) == 4>(a.p[2], a.v[2], n, i, s, Ls, v1);
             R d = 0;
 #pragma unroll
             for (int r = 0; r < 24; r++) d += v1[r] * v1[r];
@@ -219,18 +220,18 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
         } else if constexpr (OP == BLAS_RESIDUAL) {
             // v0 = v1 - v2 ; optional copy into v3 ; |v0|^2
             R v1[24];
-            load_any<R>(a.p[1], a.v[1], n, i, s, Ls, v1);
+            load_any<R, sizeof(R) == 4>(a.p[1], a.v[1], n, i, s, Ls, v1);
             {
                 R v2[24];
-                load_any<R>(a.p[2], a.v[2], n, i, s, Ls, v2);
+                load_any<R, sizeof(R) == 4>(a.p[2], a.v[2], n, i, s, Ls, v2);
 #pragma unroll
                 for (int r = 0; r < 24; r++) v1[r] -= v2[r];
             }
             R d = 0;
 #pragma unroll
             for (int r = 0; r < 24; r++) d += v1[r] * v1[r];
-            store_any<R>(a.p[0], a.v[0], n, i, s, Ls, v1);
-            if (a.v[3]) store_any<R>(a.p[3], a.v[3], n, i, s, Ls, v1);
+            store_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v1);
+            if (a.v[3]) store_any<R, sizeof(R) == 4>(a.p[3], a.v[3], n, i, s, Ls, v1);
             p0 = (double)d;
         }
     }
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
             R *sv = reinterpret_cast<R *>(blas_smem);
             R v[24];
             if (active) {
-                load_any<R>(a.p[0], a.v[0], n, i, s, Ls, v);
+                load_any<R, sizeof(R) == 4>(a.p[0], a.v[0], n, i, s, Ls, v);
 #pragma unroll
                 for (int r = 0; r < 24; r++) sv[(jl * Ls + s) * 24 + r] = v[r];
             }
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) blas_kernel(BlasA
                 for (int r = 0; r < 12; r++) u[r] = cb * v[r] + fp * vp[r];
 #pragma unroll
                 for (int r = 12; r < 24; r++) u[r] = cb * v[r] + fm * vm[r];
-                store_any<R>(a.mphi_prec, a.mphi_out, n, i, s, Ls, u);
+                store_any<R, sizeof(R) == 4>(a.mphi_prec, a.mphi_out, n, i, s, Ls, u);
             }
         }
     }
@@ -596,6 +597,105 @@ void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, i
         pout, out, Ls_out, pin, in, Ls_in, T, nsite, dagger, addv, padd, add_coef, tile);
     DWF_CUDA(cudaGetLastError());
     count_launch();
+}
+
+// ------------------------------------------------ transform contraction
+// G[(s*4+mu)][(t*4+nu)] = sum over sites x and colours c of
+//   a[s][x][mu][c] * conj(b[t][x][nu][c])
+// for canonical FP64 fields a (La slices) and b (Lb slices): the outer
+// products that make the gradient of the reduced-Ls loss (Sec. 3.3).  A fixed
+// grid of CTAs strides over chunks of sites, each writing its partial matrix;
+// a second kernel sums the partials in a fixed order (deterministic).
+constexpr int kContractCtas = 304, kContractSites = 8, kContractThreads = 256, kContractMaxP = 16;
+
+__global__ void __launch_bounds__(kContractThreads) tcontract_kernel(const double2 *a, int La,
+                                                                      const double2 *b, int Lb, long Vh,
+                                                                      double2 *part)
+{
+    extern __shared__ __align__(16) double2 sm_c[];
+    const int na = La * 12, nb = Lb * 12, npair = 16 * La * Lb, ncol = 4 * Lb;
+    double2 *sa = sm_c, *sb = sm_c + kContractSites * na;
+    double ar[kContractMaxP], ai[kContractMaxP];
+#pragma unroll
+    for (int k = 0; k < kContractMaxP; k++) ar[k] = ai[k] = 0.0;
+    const int tid = threadIdx.x;
+    for (long x0 = (long)blockIdx.x * kContractSites; x0 < Vh; x0 += (long)gridDim.x * kContractSites) {
+        for (int e = tid; e < kContractSites * na; e += kContractThreads) {
+            const int j = e / na, q = e - j * na, sl = q / 12, rest = q - sl * 12;
+            const long x = x0 + j;
+            sa[e] = x < Vh ? a[((long)sl * Vh + x) * 12 + rest] : make_double2(0.0, 0.0);
+        }
+        for (int e = tid; e < kContractSites * nb; e += kContractThreads) {
+            const int j = e / nb, q = e - j * nb, sl = q / 12, rest = q - sl * 12;
+            const long x = x0 + j;
+            sb[e] = x < Vh ? b[((long)sl * Vh + x) * 12 + rest] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kContractMaxP; k++) {
+            const int pr = tid + k * kContractThreads;
+            if (pr >= npair) break;
+            const int row = pr / ncol, col = pr - row * ncol;
+            const int oa = (row >> 2) * 12 + (row & 3) * 3, ob = (col >> 2) * 12 + (col & 3) * 3;
+            double rr = ar[k], ii = ai[k];
+            for (int j = 0; j < kContractSites; j++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const double2 u = sa[j * na + oa + c], v = sb[j * nb + ob + c];
+                    rr += u.x * v.x + u.y * v.y;   // u conj(v)
+                    ii += u.y * v.x - u.x * v.y;
+                }
+            ar[k] = rr;
+            ai[k] = ii;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < kContractMaxP; k++) {
+        const int pr = tid + k * kContractThreads;
+        if (pr < npair) part[(size_t)blockIdx.x * npair + pr] = make_double2(ar[k], ai[k]);
+    }
+}
+
+__global__ void tcontract_reduce(const double2 *part, int nctas, int npair, double2 *G)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= npair) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < nctas; k++) {
+        const double2 v = part[(size_t)k * npair + pr];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    G[pr] = s;
+}
+
+size_t tcontract_workspace_bytes(int La, int Lb)
+{
+    return (size_t)(kContractCtas + 1) * 16 * La * Lb * sizeof(double2);
+}
+
+void launch_tcontract(double *G_dev, const double *a, int La, const double *b, int Lb, long Vh,
+                      void *work, cudaStream_t st)
+{
+    if (La < 1 || Lb < 1 || La * Lb > kContractThreads * kContractMaxP / 16)
+        throw std::runtime_error("transform contraction: 16 La Lb must not exceed 4096");
+    const int npair = 16 * La * Lb;
+    const size_t smem = (size_t)kContractSites * 12 * (La + Lb) * sizeof(double2);
+    static bool attr = false;
+    if (!attr) {
+        DWF_CUDA(cudaFuncSetAttribute(tcontract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        attr = true;
+    }
+    double2 *part = reinterpret_cast<double2 *>(work);
+    tcontract_kernel<<<kContractCtas, kContractThreads, smem, st>>>(
+        reinterpret_cast<const double2 *>(a), La, reinterpret_cast<const double2 *>(b), Lb, Vh, part);
+    DWF_CUDA(cudaGetLastError());
+    tcontract_reduce<<<(npair + 255) / 256, 256, 0, st>>>(part, kContractCtas, npair,
+                                                          reinterpret_cast<double2 *>(G_dev));
+    DWF_CUDA(cudaGetLastError());
+    count_launch(2);
 }
 
 }  // namespace dwf

@@ -162,6 +162,11 @@ void launch_scalar(ScalarOp op, const ScalarArgs &a, cudaStream_t st);
 void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
                    const float *T, long nsite, int dagger, const void *addv, Prec padd,
                    double add_coef, cudaStream_t st);
+// G (device, (4 La) x (4 Lb) complex) = sum over sites and colours of a b^+
+// for canonical FP64 fields; work: tcontract_workspace_bytes(La, Lb) bytes.
+size_t tcontract_workspace_bytes(int La, int Lb);
+void launch_tcontract(double *G_dev, const double *a, int La, const double *b, int Lb, long Vh,
+                      void *work, cudaStream_t st);
 
 // Process-wide launch counter (every launch_* adds its kernels).
 void count_launch(long long n = 1);

@@ -174,5 +174,7 @@ dwf_status solve(Engine &E, double *const *xs, const double *const *bs, const dw
                  bool precond, SolveResult &res, std::string &err);
 // z = M^-1 r for FP64 canonical fields (single system)
 void precondition_fp64(Engine &E, double *z, const double *r, const dwf_solver_params &p);
+void reduced_local_inverse(Engine &E, double *out, const double *in, int Ls_hat, int iters,
+                           const dwf_solver_params &P);
 
 }  // namespace dwf

@@ -104,17 +104,18 @@ struct Ctx {
     double *part;
 };
 
-// z = M^-1 r (outer precision po for r and z).  The blocks may be processed
-// in waves (all k inner iterations of one wave before the next); a wave whose
-// working set fits in L2 keeps the inner iterations off HBM.  The block-major
-// site order makes every wave a contiguous site range.
-void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
+// k iterations of CG, x0 = 0, on every block's local operator A_s at fifth
+// extent L (Sec. 2.4, the inner solves), inner storage in P.inner_prec:
+// z = CG_k((+)_s A_s) rhs.  rhs: packed, precision prhs, extent L (it may be
+// the inner residual workspace itself); z: packed, precision pz, extent L.
+// The blocks may be processed in waves (all k inner iterations of one wave
+// before the next); the block-major site order makes every wave a contiguous
+// site range.
+static void inner_cg(Ctx &c, int L, const void *rhs, Prec prhs, void *z, Prec pz, int iters)
 {
     Engine &E = c.E;
     const dwf_solver_params &P = c.P;
     const Prec pi = (Prec)P.inner_prec;
-    const bool red = P.use_reduced_ls && E.Ls_hat > 0;
-    const int L = red ? E.Ls_hat : E.Ls;
     const long n = c.n;
     void *rin = E.ws("in_r", field_bytes(pi, n, L));
     void *pin = E.ws("in_p", field_bytes(pi, n, L));
@@ -130,8 +131,10 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
         a.mphi = mphi;
         if (!a.tile_sys) a.tile_sys = E.tsys_e;
     };
-
-    if (red) launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st);
+    // the last inner update writes z itself (single precision path) unless
+    // z is FP64; the first writes alpha p without reading z
+    const bool z_direct = z != zin && pz != P64;
+    const bool rhs_is_rin = rhs == rin;
     // default: every block in one wave (measured fastest on GB300: smaller,
     // L2-resident waves leave the latency-bound stages short of parallelism)
     const int wave = P.precond_wave > 0 ? std::min(P.precond_wave, E.nblk)
@@ -148,13 +151,14 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             t.nseg = b1 - b0;
         };
         {
+            // p = r = rhs (inner precision), u = M_phi p, |r|^2 per block
             BlasArgs a = blas(E, n, L, tsb, c.part);
             range(a);
             a.v[0] = pin;
             a.p[0] = pi;
-            a.v[1] = red ? rin : const_cast<void *>(r);
-            a.p[1] = red ? pi : po;
-            a.v[2] = red ? nullptr : rin;
+            a.v[1] = const_cast<void *>(rhs);
+            a.p[1] = prhs;
+            a.v[2] = rhs_is_rin ? nullptr : rin;
             a.p[2] = pi;
             with_u(a);
             launch_blas(BLAS_COPY, a, c.st);
@@ -163,12 +167,8 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             t.s0 = rr;
             launch_scalar(SC_SUM, t, c.st);
         }
-        // z starts at zero: the first update writes alpha p without reading z;
-        // the last one writes z in the outer precision straight into the
-        // result (FP32 outer, full Ls) and skips the r half
-        const bool z_direct = !red && po == P32;
-        for (int it = 0; it < P.inner_iters; it++) {
-            const bool last = it + 1 == P.inner_iters;
+        for (int it = 0; it < iters; it++) {
+            const bool last = it + 1 == iters;
             E.timed_begin(1 + it);
             const int tile = E.apply_local(pi, L, Apin, pin, c.part, b0, b1, uin);
             E.timed_end(1 + it);
@@ -186,7 +186,7 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             a.scal[0] = al;
             a.x_zero = it == 0;
             if (last && z_direct) {
-                a.v[4] = z; a.p[4] = po;
+                a.v[4] = z; a.p[4] = pz;
                 a.v[2] = a.v[3] = nullptr;
             }
             launch_blas(BLAS_CG_UPDATE, a, c.st);
@@ -206,17 +206,36 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
             }
         }
     }
-    inner_count += P.inner_iters;
-    if (red) {
-        launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st);
-    } else if (P.inner_iters == 0) {
-        BlasArgs a = blas(E, n, E.Ls, nullptr, nullptr);
+    if (iters == 0) {
+        BlasArgs a = blas(E, n, L, nullptr, nullptr);
         a.v[0] = z;
-        a.p[0] = po;
+        a.p[0] = pz;
         launch_blas(BLAS_AXPY_ZERO, a, c.st);
-    } else if (po != P32) {
-        launch_convert(po, z, P32, zin, n, E.Ls, c.st);
-    }  // else the last inner update wrote z
+    } else if (!z_direct && z != zin) {
+        launch_convert(pz, z, P32, zin, n, L, c.st);
+    }
+}
+
+// z = M^-1 r (outer precision po for r and z): the multi-splitting
+// preconditioner, or its reduced-Ls form z = (T^+ Mhat^-1 T + mu) r (Sec. 3.3).
+void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
+{
+    Engine &E = c.E;
+    const dwf_solver_params &P = c.P;
+    const Prec pi = (Prec)P.inner_prec;
+    const bool red = P.use_reduced_ls && E.Ls_hat > 0;
+    const long n = c.n;
+    if (red) {
+        const int L = E.Ls_hat;
+        void *rin = E.ws("in_r", field_bytes(pi, n, L));
+        void *zin = E.ws("in_z", field_bytes(P32, n, L));
+        launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st);
+        inner_cg(c, L, rin, pi, zin, P32, P.inner_iters);
+        launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st);
+    } else {
+        inner_cg(c, E.Ls, r, po, z, po, P.inner_iters);
+    }
+    inner_count += P.inner_iters;
 }
 
 // r64 = b64 - A x64 ; r = r64 (in po) ; rr (per system) on the device
@@ -568,6 +587,22 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
         return DWF_ENOCONV;
     }
     return DWF_OK;
+}
+
+// out = CG_iters(Mhat) in on canonical FP64 fields at the reduced extent
+// (the "exact" Mhat^-1 of the transform training of Sec. 3.3).
+void reduced_local_inverse(Engine &E, double *out, const double *in, int Ls_hat, int iters,
+                           const dwf_solver_params &P)
+{
+    const long n = E.ne;
+    Ctx c{E, P, E.st, n, Ls_hat, 1, E.ws_d("part", 2 * (std::max<long>((long)E.nblk * E.E2_pad, n) / 4 + 16))};
+    void *in64 = E.ws("ri_in64", field_bytes(P64, n, Ls_hat));
+    void *out32 = E.ws("ri_out32", field_bytes(P32, n, Ls_hat));
+    const LatticeGeom &g = *E.sys[0].g;
+    launch_pack(P64, in64, in, E.perm[0], g.ne(), g.Vh, Ls_hat, E.st);
+    inner_cg(c, Ls_hat, in64, P64, out32, P32, iters);
+    launch_convert(P64, in64, P32, out32, n, Ls_hat, E.st);  // (in64 reused for the result)
+    launch_unpack(P64, out, in64, E.perm[0], g.ne(), g.Vh, Ls_hat, E.st);
 }
 
 void precondition_fp64(Engine &E, double *z, const double *r, const dwf_solver_params &P)

@@ -411,3 +411,39 @@ def test_mspcg_reduces_outer_iterations(orc):
     assert cg["converged"] and ms["converged"]
     assert ms["true_res"] < 1.5e-8
     assert ms["iters"] < cg["iters"] / 2
+
+
+# ------------------------------------------------- reduced-Ls transform loss
+
+
+def test_T_loss_gradient_matches_finite_differences(orc):
+    """Sec. 3.3 loss: the analytic gradient G (d chi^2 = 2 Re <G, dT>) against
+    central differences of chi^2 along random complex directions."""
+    dims, Ls, Lh, sub = (8, 2, 2, 2), 4, 2, (4, 2, 2, 2)
+    o, _ = make(orc, dims, Ls, eps=0.5, mass=0.1)
+    rng = np.random.default_rng(7)
+    vs = [rnd(o.cb_shape(), 11), rnd(o.cb_shape(), 12)]
+    T = rng.standard_normal((4 * Lh, 4 * Ls)) + 1j * rng.standard_normal((4 * Lh, 4 * Ls))
+    mu = 0.3
+    chi2, G = o.T_loss(T, mu, vs, sub, Lh)
+    assert chi2 > 0
+    for seed in (1, 2):
+        D = np.random.default_rng(seed).standard_normal(T.shape) + 1j * np.random.default_rng(seed + 9).standard_normal(T.shape)
+        h = 1e-4
+        cp, _ = o.T_loss(T + h * D, mu, vs, sub, Lh, grad=False)
+        cm, _ = o.T_loss(T - h * D, mu, vs, sub, Lh, grad=False)
+        fd = (cp - cm) / (2 * h)
+        an = 2 * np.real(np.vdot(G, D))
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_T_loss_vanishes_at_identity(orc):
+    """With Ls_hat = Ls, T = 1 and mu = 0 the reduced preconditioner is M^-1
+    itself: chi^2 = 0 and the gradient vanishes."""
+    dims, Ls, sub = (8, 2, 2, 2), 4, (4, 2, 2, 2)
+    o, _ = make(orc, dims, Ls, eps=0.5, mass=0.1)
+    vs = [rnd(o.cb_shape(), 21)]
+    chi2, G = o.T_loss(np.eye(4 * Ls, dtype=np.complex128), 0.0, vs, sub, Ls)
+    vv = sum(np.vdot(v, v).real for v in vs)
+    assert chi2 <= 1e-20 * vv
+    assert np.abs(G).max() <= 1e-9 * np.sqrt(vv)
