@@ -125,3 +125,38 @@ def test_truncated_local_operator(orc, name, prec):
     B.dwf_set_local_truncated(lat.h, 0)
     e = relerr(to_numpy(lat.apply("local", xd, prec)), want_s)
     assert e < TOL[prec], f"snake {name} {prec}: {e:.3e}"
+
+
+@pytest.mark.gpu
+def test_long_fifth_dimension_runtime_path(orc):
+    """Ls = 20 (no compile-time instance): FP32 / FP64 operators against the
+    oracle; the 16-bit tensor-core stages need Ls <= 16 and say so."""
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import Lattice, to_device, to_numpy
+    dims, Ls, sub = (8, 4, 4, 4), 20, (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, 0.5, 8)
+    lat = Lattice(dims, Ls, 1.5, 0.5, 1.8, 0.02, U, sub)
+    o = orc.Oracle(dims, Ls, 1.5, 0.5, 1.8, 0.02, U)
+    x = inputs.gaussian_spinor_cb(dims, Ls, 77)
+    for prec in ("f64", "f32"):
+        xd = to_device(x, prec)
+        xin = to_numpy(xd)
+        for op, want in (("DdagD", o.DdagD(xin)), ("local", o.local_DdagD(xin, sub))):
+            e = relerr(to_numpy(lat.apply(op, xd, prec)), want)
+            assert e < TOL[prec], (prec, op, e)
+    with pytest.raises(B.DwfError):
+        lat.apply("DdagD", to_device(x, "f16"), "f16")
+
+
+@pytest.mark.gpu
+def test_kernel_config_validation(orc):
+    from paper_2104_05615_gb300 import binding as B
+    lat, o, x, sub = setup_case(orc, "part_x")
+    for tile, gather in ((6, 0), (3, 0), (8, 2), (0, 0)):
+        with pytest.raises(B.DwfError) as e:
+            B.dwf_set_kernel_config(lat.h, B.DWF_F32, 0, tile, gather)
+        assert e.value.status == B.DWF_EINVAL
+    B.dwf_set_kernel_config(lat.h, B.DWF_F32, 0, 8, 0)
+    c = B.dwf_kernel_config()
+    B.check(B.lib().dwf_get_kernel_config(lat.h, B.DWF_F32, 0, B.C.byref(c)), lat.h)
+    assert (c.tile_sites, c.gather) == (8, 0)
