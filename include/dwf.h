@@ -72,7 +72,9 @@ typedef struct {
     double tol;            /* stop when ||b - D^+D x|| / ||b|| <= tol (FP64, verified) */
     int maxiter;           /* outer iteration cap */
     int inner_iters;       /* k: fixed inner CG iterations of the preconditioner (Sec. 2.5) */
-    dwf_prec outer_prec;   /* DWF_F64 or DWF_F32 (FP32 iterations + FP64 reliable updates) */
+    dwf_prec outer_prec;   /* outer vectors: DWF_F64, DWF_F32, or DWF_F16 / DWF_BF16 (16-bit
+                              iterations as in Sec. 3.2; the solution increment stays FP32);
+                              below FP64 with FP64 reliable updates */
     dwf_prec inner_prec;   /* DWF_F32, DWF_F16 or DWF_BF16 storage for the inner solves */
     double delta;          /* reliable update when ||r|| < delta * max ||r|| since the last one */
     int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */

@@ -297,10 +297,9 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     const int Ls = E.Ls;
     const int nsys = (int)E.sys.size();
     const Prec po = (Prec)P.outer_prec;
-    if (po != P64 && po != P32) {
-        err = "outer precision must be FP64 or FP32";
-        return DWF_EINVAL;
-    }
+    // 16-bit outer vectors (the paper's 16-bit outer iterations, Sec. 3.2)
+    // keep the solution increment in FP32 between reliable updates
+    const Prec pacc = po == P64 ? P64 : P32;
     if (use_precond && (P.inner_prec == DWF_F64 || P.inner_iters < 0)) {
         err = "inner precision must be FP32, FP16 or BF16 and k >= 0";
         return DWF_EINVAL;
@@ -322,7 +321,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     void *p = E.ws("p_o", field_bytes(po, n, Ls));
     void *Ap = E.ws("Ap_o", field_bytes(po, n, Ls));
     void *z = use_precond ? E.ws("z_o", field_bytes(po, n, Ls)) : r;
-    void *xacc = po == P64 ? x64 : E.ws("xacc_o", field_bytes(po, n, Ls));
+    void *xacc = po == P64 ? x64 : E.ws("xacc_o", field_bytes(pacc, n, Ls));
     void *u = E.ws("u_o", field_bytes(po, n, Ls));  // M_phi p, written with p
     const double *mphi_o = E.mats(Ls).mphi;
     auto with_u = [&](BlasArgs &a) {
@@ -361,7 +360,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     if (po != P64) {
         BlasArgs a = blas(E, n, Ls, nullptr, nullptr);
         a.v[0] = xacc;
-        a.p[0] = po;
+        a.p[0] = pacc;
         launch_blas(BLAS_AXPY_ZERO, a, st);
     }
     DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
@@ -425,7 +424,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             launch_scalar(SC_ALPHA, s, st);
         }
         BlasArgs a = blas(E, n, Ls, E.seg_sys.d_tile_seg, c.part);
-        a.v[0] = xacc; a.p[0] = po;
+        a.v[0] = xacc; a.p[0] = pacc;
         a.v[1] = p; a.p[1] = po;
         a.v[2] = r; a.p[2] = po;
         a.v[3] = Ap; a.p[3] = po;
@@ -515,7 +514,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
             }
         }
         if (do_ru) {
-            launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);
+            launch_accum(x64, xacc, pacc, n, Ls, kBlasTile, st);
             true_residual(c, po, x64, b64, Ax64, r64, r, rr);
             DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
             DWF_CUDA(cudaStreamSynchronize(st));
@@ -547,7 +546,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     }
     // final solution and FP64 true residual (every system)
     E.active = nullptr;
-    if (po != P64) launch_accum(x64, xacc, po, n, Ls, kBlasTile, st);
+    if (po != P64) launch_accum(x64, xacc, pacc, n, Ls, kBlasTile, st);
     true_residual(c, po, x64, b64, Ax64, r64, r, rr);
     for (int k = 0; k < nsys; k++) {
         const LatticeGeom &g = *E.sys[k].g;

@@ -174,3 +174,16 @@ def test_live_operator_timing(orc, graph):
     assert 0 < st.outer_op_ms / st.outer_op_count < 50
     assert 0 < st.local_op_ms / st.local_op_count < 50
     assert st.local_op_ms < st.time_total_ms
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("outer", ["f16", "bf16"])
+@pytest.mark.parametrize("mspcg", [True, False])
+def test_16bit_outer_iterations(orc, outer, mspcg):
+    """16-bit outer vectors (Sec. 3.2: 16-bit outer iterations with FP64
+    reliable updates) reach the FP64 tolerance."""
+    lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
+    x, st = lat.solve(torch.from_numpy(b).cuda(), mspcg=mspcg, tol=1e-10, outer_prec=outer,
+                      inner_prec="f16", maxiter=20000)
+    assert st["converged"] and st["reliable_updates"] >= 1
+    assert o.true_residual(x.cpu().numpy(), b) <= 1e-10 * 1.01
