@@ -60,3 +60,32 @@ def test_c4_size_operator_identities():
     assert xAx.real > 0 and abs(xAx.imag) < 1e-5 * xAx.real   # positive
     nDx = vd(Dx, Dx).real
     assert abs(xAx.real - nDx) < 1e-5 * nDx          # <x, D^+D x> = |Dx|^2
+
+
+@pytest.mark.gpu
+def test_batched_workload_full_size_sampled(orc):
+    """The 48-lattice batched workload at full size in one dwf_batch_mspcg call
+    (the bench's launch configuration); one system of each shape verified with
+    the oracle's FP64 true residual, every system with the solver's own."""
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import Lattice, PREC
+    systems = inputs.c5_systems()
+    lats, bs, xs = [], [], []
+    for c in systems:
+        U = inputs.gauge_field(c["dims"], c["eps"], c["gauge_seed"])
+        lats.append(Lattice(c["dims"], c["Ls"], c["b"], c["c"], c["M5"], c["mass"], U, c["sub"]))
+        bs.append(torch.from_numpy(inputs.gaussian_spinor_cb(c["dims"], c["Ls"], c["src_seed"])).cuda())
+        xs.append(torch.zeros_like(bs[-1]))
+    bt = B.dwf_batch_create([l.h for l in lats])
+    try:
+        tot, per = B.dwf_batch_mspcg(bt, xs, bs, B.default_params(tol=1e-9, inner_iters=6,
+                                                                  inner_prec=PREC["f16"], maxiter=100000))
+        assert tot.converged
+        assert max(q.true_residual for q in per) <= 1e-9
+        for k in (0, 16, 47):  # 8^4, 8^3x16, 12^4
+            c = systems[k]
+            U = inputs.gauge_field(c["dims"], c["eps"], c["gauge_seed"])
+            o = orc.Oracle(c["dims"], c["Ls"], c["b"], c["c"], c["M5"], c["mass"], U)
+            assert o.true_residual(xs[k].cpu().numpy(), bs[k].cpu().numpy()) <= 1e-9 * 1.01, k
+    finally:
+        B.dwf_batch_destroy(bt)
