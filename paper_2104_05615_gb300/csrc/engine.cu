@@ -364,6 +364,7 @@ const Mats &Engine::mats(int L)
     for (auto &hk : h) hk.assign(per * sys.size(), 0.0);
     std::vector<double> mp;
     const double A = b * (4.0 - M5) + 1.0, B = c * (4.0 - M5) - 1.0;
+    m.structured = A != 0.0 && std::fabs(B / A) < 0.9;
     for (size_t k = 0; k < sys.size(); k++) {
         const double mass = sys[k].mass;
         mp.push_back(b);
@@ -463,6 +464,14 @@ static void set_mats(StageArgs &a, const Mats &m, Prec p, MatKind f, MatKind g, 
     } else {
         a.F = matp(m, f, p);
         a.G = (g == MK_N) ? nullptr : matp(m, g, p);
+        a.fprog = FP_DENSE;
+        if (m.structured && m.Ls <= 32) {
+            if (f == MK_S1F && g == MK_N) a.fprog = FP_S1;
+            else if (f == MK_S3F && g == MK_N) a.fprog = FP_S3;
+            else if (f == MK_M5I && g == MK_N) a.fprog = FP_M5I;
+            else if (f == MK_M5ID && g == MK_N) a.fprog = FP_M5ID;
+            else if (f == MK_S2GF && g == MK_M5ID) a.fprog = FP_S2;
+        }
     }
 }
 
@@ -473,6 +482,7 @@ void Engine::apply_5d(Prec p, int L, MatKind k, void *out, const void *in, long 
     a.err = err_flag;
     a.in = in;
     a.out = out;
+    a.mphi = m.mphi;
     set_mats(a, m, p, k, MK_N, k == MK_M5I ? TC_M5I : TC_M5ID);
     a.tile_sys = (nsite == ne) ? tsys_e : nullptr;
     a.nout = nsite;
@@ -711,6 +721,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b3.err = err_flag;
     b3.gather = kc.gather;
     b3.active = active;
+    b3.mphi = m.mphi;
     b3.Ls = L;
     b3.tile = tile;
     b3.in = wv;

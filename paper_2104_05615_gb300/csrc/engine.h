@@ -38,6 +38,7 @@ enum TcKind {
 };
 struct Mats {
     int Ls = 0;
+    bool structured = false;  // |B / A| < 0.9: the recurrences of FProg are well damped
     double *d64[MK_N] = {};
     float *d32[MK_N] = {};
     void *tc[TC_N] = {};

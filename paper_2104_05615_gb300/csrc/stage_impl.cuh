@@ -289,6 +289,62 @@ __device__ __forceinline__ void ldmatrix_x4_trans(uint32_t addr, uint32_t &r0, u
                  : "r"(addr));
 }
 
+// Fifth-dimension structure (Sec. 2.2): M5op = A + B P with P a one-step
+// shift in s, "up" ((P y)_s = y_{s+1}, (P y)_{L-1} = -mass y_0; chirality 0)
+// or "down" ((P y)_s = y_{s-1}, (P y)_0 = -mass y_{L-1}; chirality 1); P^T
+// swaps the two.  (A + B P)^-1 x: the first element (in the recurrence's
+// order) from the closed form of the inverse's first row, then
+// y_s = x_s / A + q y_{s-+1}, q = -B/A (|q| < 0.9 is checked on the host, so
+// the recurrence damps rounding).  In place on the column x[0..L).
+template <typename R, int L>
+__device__ __forceinline__ void m5_solve(R *x, bool up, R A, R q, R mass)
+{
+    const R invA = R(1) / A;
+    R qL = R(1);
+#pragma unroll
+    for (int t = 0; t < L; t++) qL *= q;
+    const R invAd = invA / (R(1) + mass * qL);
+    R S = R(0);
+    if (!up) {
+#pragma unroll
+        for (int t = 1; t < L; t++) S = q * S + x[t];
+        R y = (x[0] - mass * q * S) * invAd;
+        x[0] = y;
+#pragma unroll
+        for (int t = 1; t < L; t++) {
+            y = x[t] * invA + q * y;
+            x[t] = y;
+        }
+    } else {
+#pragma unroll
+        for (int t = L - 2; t >= 0; t--) S = q * S + x[t];
+        R y = (x[L - 1] - mass * q * S) * invAd;
+        x[L - 1] = y;
+#pragma unroll
+        for (int t = L - 2; t >= 0; t--) {
+            y = x[t] * invA + q * y;
+            x[t] = y;
+        }
+    }
+}
+
+// M_phi x = (hb + hc P) x with hb = -b/2, hc = -c/2, in place.
+template <typename R, int L>
+__device__ __forceinline__ void mphi_apply(R *x, bool up, R hb, R hc, R mass)
+{
+    if (up) {
+        const R y0 = x[0];
+#pragma unroll
+        for (int t = 0; t < L - 1; t++) x[t] = hb * x[t] + hc * x[t + 1];
+        x[L - 1] = hb * x[L - 1] - hc * mass * y0;
+    } else {
+        const R yl = x[L - 1];
+#pragma unroll
+        for (int t = L - 1; t >= 1; t--) x[t] = hb * x[t] + hc * x[t - 1];
+        x[0] = hb * x[0] - hc * mass * yl;
+    }
+}
+
 // Shared-memory layout of a stage CTA (byte offsets), shared by host and device.
 struct StageSmem {
     int bar, nbr, smax, lraw, U, mat, col, scl, aux, auxs, dot, dots, H, A, D, total;
@@ -871,13 +927,62 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
         // ---------------------------------------------------------------
         // CUDA-core path (FP32 / FP64)
         const R *sF = sX, *sG = sX + 2 * Ls * Ls;
+        // (the structured programs read the per-system b, c, mass, A, B)
+        const bool structured = LS > 0 && a.fprog != FP_DENSE && a.mphi != nullptr;
         if (active) {
             store24(sH + (jl * Ls + s) * 24, acc);
-            if (kAux && a.G) store24(sA + (jl * Ls + s) * 24, av);
+            if (kAux && (a.G || structured)) store24(sA + (jl * Ls + s) * 24, av);
         }
         __syncthreads();
+        if constexpr (LS > 0) {
+            if (structured) {
+                // one thread per (site, real component) runs the column's
+                // fifth-dimension program in place, then every (site, s)
+                // thread reads its 24 outputs back
+                const double *mp = a.mphi + 5 * sys;
+                const R hb = (R)(-0.5 * mp[0]), hc = (R)(-0.5 * mp[1]), mass = (R)mp[2];
+                const R A5 = (R)mp[3], q = (R)(-mp[4] / mp[3]);
+                for (int col = tid; col < TS * 24; col += nthr) {
+                    const int j = col / 24, r = col - j * 24;
+                    const bool up = r < 12;  // chirality 0: spins 0, 1
+                    R x[LS];
+#pragma unroll
+                    for (int t = 0; t < LS; t++) x[t] = sH[(j * LS + t) * 24 + r];
+                    switch (a.fprog) {
+                    case FP_S1:
+                        m5_solve<R, LS>(x, up, A5, q, mass);
+                        mphi_apply<R, LS>(x, up, hb, hc, mass);
+                        break;
+                    case FP_S3:
+                        mphi_apply<R, LS>(x, !up, hb, hc, mass);
+                        m5_solve<R, LS>(x, !up, A5, q, mass);
+                        break;
+                    case FP_M5I: m5_solve<R, LS>(x, up, A5, q, mass); break;
+                    case FP_M5ID: m5_solve<R, LS>(x, !up, A5, q, mass); break;
+                    default:  // FP_S2
+                        m5_solve<R, LS>(x, up, A5, q, mass);
+#pragma unroll
+                        for (int t = 0; t < LS; t++) x[t] = sA[(j * LS + t) * 24 + r] - x[t];
+                        m5_solve<R, LS>(x, !up, A5, q, mass);
+                        break;
+                    }
+                    if (kMode == MODE_S2 && a.fprog != FP_S2) {
+                        // G null: aux - F h
+#pragma unroll
+                        for (int t = 0; t < LS; t++) x[t] = sA[(j * LS + t) * 24 + r] - x[t];
+                    }
+#pragma unroll
+                    for (int t = 0; t < LS; t++) sH[(j * LS + t) * 24 + r] = x[t];
+                }
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < 24; r++) out[r] = sH[(jl * Ls + s) * 24 + r];
+                }
+            }
+        }
         const R *Hsite = sH + jl * Ls * 24;
-        if (active) {
+        if (active && !structured) {
             if (kMode == MODE_F || kMode == MODE_5D) {
                 apply5<R, false>(sF, Hsite, Ls, s, out, R(1));
             } else {
@@ -987,7 +1092,10 @@ void launch_stage_prec(StageMode mode, bool mphi, const StageArgs &a, cudaStream
         return;
     }
     if constexpr (T::P == P64) {
-        dispatch_mode<T, false, 0, 0>(mode, mphi, a, st);
+        // compile-time fifth extent for the reliable updates' common Ls
+        if (a.Ls == 12) dispatch_mode<T, false, 12, 0>(mode, mphi, a, st);
+        else if (a.Ls == 16) dispatch_mode<T, false, 16, 0>(mode, mphi, a, st);
+        else dispatch_mode<T, false, 0, 0>(mode, mphi, a, st);
     } else {
         switch (a.Ls) {
         case 4: dispatch_mode<T, false, 4, 0>(mode, mphi, a, st); break;
