@@ -76,10 +76,10 @@ struct StageArgs {
 };
 
 // The fifth-dimension operators of a CUDA-core stage as structured solves
-// (M5op = A + B P is bidiagonal up to one wrap term, M_phi = -(b + c P)/2):
-// FP_S1 M_phi M5^-1, FP_S3 M5^-+ M_phi^+, FP_M5I M5^-1, FP_M5ID M5^-+,
-// FP_S2 M5^-+ (aux - M5^-1 h).  FP_DENSE applies the dense F (and G).
-enum FProg { FP_DENSE = 0, FP_S1, FP_S3, FP_M5I, FP_M5ID, FP_S2 };
+// (M5op = A + B P is bidiagonal up to one wrap term): FP_M5I M5^-1,
+// FP_M5ID M5^-+, FP_S2 M5^-+ (aux - M5^-1 h).  FP_DENSE applies the dense F
+// (and G).
+enum FProg { FP_DENSE = 0, FP_M5I, FP_M5ID, FP_S2 };
 
 // Does a (tile, gather) choice fit the per-CTA limits for this precision and Ls?
 bool stage_fits(Prec prec, int tile, int Ls, int gather);

@@ -465,10 +465,10 @@ static void set_mats(StageArgs &a, const Mats &m, Prec p, MatKind f, MatKind g, 
         a.F = matp(m, f, p);
         a.G = (g == MK_N) ? nullptr : matp(m, g, p);
         a.fprog = FP_DENSE;
+        // structured where it beats the dense product (measured: S2's two
+        // products; a single F product in S1 / S3 is as fast dense)
         if (m.structured && m.Ls <= 32) {
-            if (f == MK_S1F && g == MK_N) a.fprog = FP_S1;
-            else if (f == MK_S3F && g == MK_N) a.fprog = FP_S3;
-            else if (f == MK_M5I && g == MK_N) a.fprog = FP_M5I;
+            if (f == MK_M5I && g == MK_N) a.fprog = FP_M5I;
             else if (f == MK_M5ID && g == MK_N) a.fprog = FP_M5ID;
             else if (f == MK_S2GF && g == MK_M5ID) a.fprog = FP_S2;
         }

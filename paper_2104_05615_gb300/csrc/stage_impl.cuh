@@ -328,23 +328,6 @@ __device__ __forceinline__ void m5_solve(R *x, bool up, R A, R q, R mass)
     }
 }
 
-// M_phi x = (hb + hc P) x with hb = -b/2, hc = -c/2, in place.
-template <typename R, int L>
-__device__ __forceinline__ void mphi_apply(R *x, bool up, R hb, R hc, R mass)
-{
-    if (up) {
-        const R y0 = x[0];
-#pragma unroll
-        for (int t = 0; t < L - 1; t++) x[t] = hb * x[t] + hc * x[t + 1];
-        x[L - 1] = hb * x[L - 1] - hc * mass * y0;
-    } else {
-        const R yl = x[L - 1];
-#pragma unroll
-        for (int t = L - 1; t >= 1; t--) x[t] = hb * x[t] + hc * x[t - 1];
-        x[0] = hb * x[0] - hc * mass * yl;
-    }
-}
-
 // Shared-memory layout of a stage CTA (byte offsets), shared by host and device.
 struct StageSmem {
     int bar, nbr, smax, lraw, U, mat, col, scl, aux, auxs, dot, dots, H, A, D, total;
@@ -940,8 +923,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
                 // fifth-dimension program in place, then every (site, s)
                 // thread reads its 24 outputs back
                 const double *mp = a.mphi + 5 * sys;
-                const R hb = (R)(-0.5 * mp[0]), hc = (R)(-0.5 * mp[1]), mass = (R)mp[2];
-                const R A5 = (R)mp[3], q = (R)(-mp[4] / mp[3]);
+                const R mass = (R)mp[2], A5 = (R)mp[3], q = (R)(-mp[4] / mp[3]);
                 for (int col = tid; col < TS * 24; col += nthr) {
                     const int j = col / 24, r = col - j * 24;
                     const bool up = r < 12;  // chirality 0: spins 0, 1
@@ -949,14 +931,6 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
 #pragma unroll
                     for (int t = 0; t < LS; t++) x[t] = sH[(j * LS + t) * 24 + r];
                     switch (a.fprog) {
-                    case FP_S1:
-                        m5_solve<R, LS>(x, up, A5, q, mass);
-                        mphi_apply<R, LS>(x, up, hb, hc, mass);
-                        break;
-                    case FP_S3:
-                        mphi_apply<R, LS>(x, !up, hb, hc, mass);
-                        m5_solve<R, LS>(x, !up, A5, q, mass);
-                        break;
                     case FP_M5I: m5_solve<R, LS>(x, up, A5, q, mass); break;
                     case FP_M5ID: m5_solve<R, LS>(x, !up, A5, q, mass); break;
                     default:  // FP_S2
