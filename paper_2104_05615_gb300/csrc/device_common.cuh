@@ -165,7 +165,7 @@ __device__ __forceinline__ void store_sp<TF16>(void *base, long nsite, long site
 #pragma unroll
     for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
     const float sc = m > 0.f ? m : 1.f;
-    const float inv = 1.f / sc;
+    const float inv = __fdividef(1.f, sc);  // stored value x scale = v to well within FP16 rounding
     float w[24];
 #pragma unroll
     for (int i = 0; i < 24; i++) w[i] = v[i] * inv;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void store_sp_scaled(void *base, long nsite, long sit
 #pragma unroll
     for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
     const float sc = m > 0.f ? m : 1.f;
-    const float inv = 1.f / sc;
+    const float inv = __fdividef(1.f, sc);  // stored value x scale = v to well within FP16 rounding
     float w[24];
 #pragma unroll
     for (int i = 0; i < 24; i++) w[i] = v[i] * inv;

@@ -745,14 +745,15 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
             const R cA = a.G ? (R)mp[3] : R(1), cB = a.G ? (R)mp[4] : R(0);
             const int sm = s > 0 ? s - 1 : Ls - 1, sp = s + 1 < Ls ? s + 1 : 0;
             const R flo = s > 0 ? R(1) : -mass, fhi = s + 1 < Ls ? R(1) : -mass;
-            const R *H0 = sH + (jl * Ls + s) * 24, *A0 = sA + (jl * Ls + s) * 24;
+            // the thread's own slice from registers, the neighbouring slices' halves
+            // from shared memory
             const R *Hm = sH + (jl * Ls + sm) * 24, *Am = sA + (jl * Ls + sm) * 24;
             const R *Hp = sH + (jl * Ls + sp) * 24, *Ap = sA + (jl * Ls + sp) * 24;
             const R bl = cB * flo, cl = hc * flo, bh = cB * fhi, ch = hc * fhi;
 #pragma unroll
-            for (int r = 0; r < 12; r++) out[r] = cA * A0[r] + bl * Am[r] + hb * H0[r] + cl * Hm[r];
+            for (int r = 0; r < 12; r++) out[r] = cA * av[r] + bl * Am[r] + hb * acc[r] + cl * Hm[r];
 #pragma unroll
-            for (int r = 12; r < 24; r++) out[r] = cA * A0[r] + bh * Ap[r] + hb * H0[r] + ch * Hp[r];
+            for (int r = 12; r < 24; r++) out[r] = cA * av[r] + bh * Ap[r] + hb * acc[r] + ch * Hp[r];
         }
     } else if constexpr (kTC) {
         // ---------------------------------------------------------------
@@ -764,6 +765,9 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
         // with ldmatrix.trans; D is rescaled by the same factor.
         const int RS = kTcRow(TS);
         constexpr int nk = kAux ? 2 : 1;
+        // S2 reads aux only on the block interior, which comes first in E2: a
+        // tile whose first site lies beyond it has no aux and skips that k-step
+        const bool aux_tile = kAux && (kMode == MODE_S4 || (int)(i0 - (long)seg * a.seg_out) < a.aux_valid);
         __half *sB = reinterpret_cast<__half *>(smem_raw + L.H);
         if (active) {
             float m = 0.f;
@@ -788,7 +792,8 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
         __syncthreads();
         if (active) {
             const float sig = sMax[jl];
-            const float inv = sig > 0.f ? 1.f / sig : 0.f;
+            // any factor within a few ulp of 1/sig keeps the FP16 operands in range
+            const float inv = sig > 0.f ? __fdividef(1.f, sig) : 0.f;
             auto put = [&](__half *tile, const R *v) {
 #pragma unroll
                 for (int chi = 0; chi < 2; chi++) {
@@ -801,7 +806,9 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
                 }
             };
             // tile 0: aux (if any) else h ; tile 1: h
-            if constexpr (kAuxRaw) {
+            if (kAux && !aux_tile) {
+                put(sB + (size_t)2 * 16 * RS, acc);
+            } else if constexpr (kAuxRaw) {
                 // stored halves times (aux scale / site scale) <= 1
                 const __half2 r2 = __float2half2_rn(asc * inv);
                 auto mul = [&](uint32_t w) {
@@ -848,6 +855,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
             for (int q = 0; q < 8; q++) d[q] = 0.f;
 #pragma unroll
             for (int kk = 0; kk < nk; kk++) {
+                if (kAux && kk == 0 && !aux_tile) continue;  // aux all zero in this tile
                 const __half *tb = sB + ((size_t)(kk * 2 + chi) * 16 + lr) * RS + pr * 16 + ln;
                 uint32_t b0, b1, b2, b3;
                 ldmatrix_x4_trans(smem_u32(tb), b0, b1, b2, b3);
