@@ -105,8 +105,8 @@ def local_op_bytes(geo, Ls, prec="f16"):
     """Compulsory bytes of one local-operator application (four hop stages):
     every input field read once, every output written once, aux fields read
     once, two rows of each of the 8 links per output 4D site read once."""
-    w = {"f16": 2 * 24 + 4, "bf16": 48, "f32": 96, "f64": 192}[prec]   # bytes / 5D site
-    wl = {"f16": 2, "bf16": 2, "f32": 4, "f64": 8}[prec] * 12 * 8      # link bytes / 4D site
+    w = {"f16": 2 * 24 + 4, "fx16": 2 * 24 + 4, "bf16": 48, "f32": 96, "f64": 192}[prec]   # bytes / 5D site
+    wl = {"f16": 2, "fx16": 2, "bf16": 2, "f32": 4, "f64": 8}[prec] * 12 * 8      # link bytes / 4D site
     nb = geo["blocks"]
     I, O1, E2 = nb * geo["block_sites"], nb * geo["o1_sites"], nb * geo["e2_sites"]
     s1 = (I + O1) * Ls * w + O1 * wl
@@ -117,8 +117,8 @@ def local_op_bytes(geo, Ls, prec="f16"):
 
 
 def global_op_bytes(geo, Ls, prec="f32"):
-    w = {"f16": 52, "bf16": 48, "f32": 96, "f64": 192}[prec]
-    wl = {"f16": 2, "bf16": 2, "f32": 4, "f64": 8}[prec] * 12 * 8
+    w = {"f16": 52, "fx16": 52, "bf16": 48, "f32": 96, "f64": 192}[prec]
+    wl = {"f16": 2, "fx16": 2, "bf16": 2, "f32": 4, "f64": 8}[prec] * 12 * 8
     n = geo["even_sites"]
     # S1: x -> t1 ; S2: t1, x -> w ; S3: w -> t3 ; S4: t3, w, x -> out
     return (2 + 3 + 2 + 4) * n * Ls * w + 4 * n * wl
@@ -137,7 +137,7 @@ def setup(cfg_name, device):
 
 
 STAGE_SOURCES = ("stage_impl.cuh", "device_common.cuh", "dwf_internal.h", "stage.cu",
-                 "stage_f16.cu", "stage_f32.cu", "stage_bf16.cu", "stage_f64.cu")
+                 "stage_f16.cu", "stage_f32.cu", "stage_bf16.cu", "stage_f64.cu", "stage_fx16.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_stage_kernels_16x16x16x32_Ls12.md")
 
 
@@ -397,6 +397,12 @@ def main():
     ap.add_argument("--op-reps", type=int, default=3)
     ap.add_argument("--kcfg", default=None,
                     help="fixed stage launch config 'tile,gather' for both operators (ops and solve modes)")
+    ap.add_argument("--op-precs", default=None,
+                    help="ops mode: also time the local operator in these storage formats")
+    ap.add_argument("--inner-precs", default="f16,bf16",
+                    help="inner mode: inner storage formats (f32, f16, bf16, fx16)")
+    ap.add_argument("--inner-ks", default="3,4,6,12,18", help="inner mode: inner iteration counts")
+    ap.add_argument("--no-ablation", action="store_true", help="inner mode: skip the truncated-operator run")
     ap.add_argument("--train-steps", type=int, default=8, help="train mode: descent steps")
     ap.add_argument("--train-mus", default=None,
                     help="train mode: comma-separated suppression factors mu (default: the workload's)")
@@ -443,8 +449,11 @@ def main():
             B.dwf_set_kernel_config(lat.h, PREC["f32"], 0, tile, gather)
         tl = time_op(lat, B.DWF_OP_LOCAL_DDAGD, inner, args.op_reps, flush)
         tg = time_op(lat, B.DWF_OP_DDAGD, "f32", args.op_reps, flush)
+        extra = {}
+        for pr in (args.op_precs.split(",") if args.op_precs else []):
+            extra[f"local_ms_{pr}"] = time_op(lat, B.DWF_OP_LOCAL_DDAGD, pr, args.op_reps, flush) * 1e3
         if rank == 0:
-            print(json.dumps({"local_ms": tl * 1e3, "global_ms": tg * 1e3}))
+            print(json.dumps({"local_ms": tl * 1e3, "global_ms": tg * 1e3, **extra}))
         return
     if args.mode == "train":
         # Sec. 3.3: train the reduced-Ls transform T on residuals of the solve
@@ -498,11 +507,15 @@ def main():
         return
     if args.mode == "inner":
         # Table 1's trend on this workload: plain CG, then MSPCG with k inner
-        # iterations in FP16 and BF16 (one warm-up and one timed solve each)
+        # iterations in each inner storage format (one warm-up and one timed
+        # solve each), then the snake-term ablation (Eq. (eq:diri))
         from paper_2104_05615_gb300.lattice import PREC
         rows = []
-        runs = [("plain", None, 0)] + [(k, pr, 0) for pr in ("f16", "bf16") for k in (3, 4, 6, 12, 18)]
-        runs.append((6, "f16", 1))  # the snake-term ablation (Eq. (eq:diri))
+        precs = args.inner_precs.split(",")
+        ks = [int(k) for k in args.inner_ks.split(",")]
+        runs = ([("plain", None, 0)] if not args.no_cg else []) + [(k, pr, 0) for pr in precs for k in ks]
+        if not args.no_ablation:
+            runs.append((6, "f16", 1))
         for k, pr, trunc in runs:
             B.dwf_set_local_truncated(lat.h, trunc)
             if k == "plain":

@@ -16,7 +16,8 @@
  *     ((s*(V/2) + lex/2)*4 + spin)*3 + colour, complex interleaved (re, im),
  *     over the sites of one parity.  Element type by precision:
  *       DWF_F64: double[2], DWF_F32: float[2], DWF_F16: IEEE half[2],
- *       DWF_BF16: bfloat16[2].
+ *       DWF_BF16: bfloat16[2], DWF_FX16: float[2] (the fixed-point format is
+ *       a device storage format only; it is exchanged as FP32).
  *   - Gauge field (host, FP64): ((lex*4 + mu)*3 + row)*3 + col complex
  *     (double[2]); mu = x, y, z, t; links must be SU(3) to ~1e-14 (the device
  *     copies keep two rows and rebuild the third).
@@ -56,7 +57,12 @@ typedef enum {
     DWF_EUNSUPPORTED = 6   /* valid but not implemented combination */
 } dwf_status;
 
-typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2, DWF_BF16 = 3 } dwf_prec;
+/* DWF_FX16: the 16-bit fixed-point format of Sec. 3.2 (Eq. for the fixed-point
+ * value): every colour-spinor (24 reals at one site and s) is stored as 24
+ * int16 integers q with one FP32 number, value = q / 32767 * max|component|
+ * (the FP32 number kept is max/32767); loads unpack to FP32 and all
+ * arithmetic is FP32, the fifth-dimension products on the tensor cores. */
+typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2, DWF_BF16 = 3, DWF_FX16 = 4 } dwf_prec;
 
 typedef enum {
     DWF_OP_D = 0,           /* D = 1 - M5^-1 M4_eo M5^-1 M4_oe (Sec. 2.2, Eq. dirac_equation) */
@@ -72,10 +78,11 @@ typedef struct {
     double tol;            /* stop when ||b - D^+D x|| / ||b|| <= tol (FP64, verified) */
     int maxiter;           /* outer iteration cap */
     int inner_iters;       /* k: fixed inner CG iterations of the preconditioner (Sec. 2.5) */
-    dwf_prec outer_prec;   /* outer vectors: DWF_F64, DWF_F32, or DWF_F16 / DWF_BF16 (16-bit
+    dwf_prec outer_prec;   /* outer vectors: DWF_F64, DWF_F32, or DWF_F16 / DWF_BF16 / DWF_FX16 (16-bit
                               iterations as in Sec. 3.2; the solution increment stays FP32);
                               below FP64 with FP64 reliable updates */
-    dwf_prec inner_prec;   /* DWF_F32, DWF_F16 or DWF_BF16 storage for the inner solves */
+    dwf_prec inner_prec;   /* DWF_F32, DWF_F16, DWF_BF16 or DWF_FX16 storage for the inner
+                              solves */
     double delta;          /* reliable update when ||r|| < delta * max ||r|| since the last one */
     int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */
     int use_graph;         /* 1: capture each outer iteration in a CUDA graph */
@@ -150,8 +157,8 @@ dwf_status dwf_unpack(dwf_handle *h, void *canonical_dev, const void *packed_dev
                       void *stream);
 
 /* out = op(in) on canonical even fields of precision prec (device buffers,
- * distinct).  FP64 and FP32 compute in their own precision; DWF_F16 and
- * DWF_BF16 store in 16 bits and compute in FP32, with the dense fifth-
+ * distinct).  FP64 and FP32 compute in their own precision; DWF_F16,
+ * DWF_BF16 and DWF_FX16 store in 16 bits and compute in FP32, with the dense fifth-
  * dimension matrices on the tensor cores.  DWF_OP_LOCAL_DDAGD uses the
  * handle's block dims. */
 dwf_status dwf_apply(dwf_handle *h, void *out_dev, const void *in_dev, dwf_op op, dwf_prec prec,

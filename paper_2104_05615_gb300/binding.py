@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libdwf_gb300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "dwf.h")
 
 DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ECUDA, DWF_ENOCONV, DWF_ETIMEOUT, DWF_EUNSUPPORTED = range(7)
-DWF_F64, DWF_F32, DWF_F16, DWF_BF16 = range(4)
+DWF_F64, DWF_F32, DWF_F16, DWF_BF16, DWF_FX16 = range(5)
 DWF_OP_D, DWF_OP_DDAG, DWF_OP_DDAGD, DWF_OP_LOCAL_DDAGD, DWF_OP_M5INV, DWF_OP_M5INVDAG = range(6)
 
 

@@ -162,7 +162,7 @@ dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g)
     return DWF_OK;
 }
 
-static bool prec_ok(int p) { return p >= DWF_F64 && p <= DWF_BF16; }
+static bool prec_ok(int p) { return p >= DWF_F64 && p <= DWF_FX16; }
 
 dwf_status dwf_pack(dwf_handle *h, void *packed, const void *canon, dwf_prec prec, void *stream)
 {
@@ -328,7 +328,7 @@ dwf_status dwf_reduced_local_inverse(dwf_handle *h, double *out, const double *i
     if (p) P = *p;
     else dwf_default_params(&P);
     if (!prec_ok(P.inner_prec) || P.inner_prec == DWF_F64) return DWF_EINVAL;
-    if ((P.inner_prec == DWF_F16 || P.inner_prec == DWF_BF16) && Ls_hat > 16) return DWF_EINVAL;
+    if (P.inner_prec >= DWF_F16 && Ls_hat > 16) return DWF_EINVAL;
     return guarded(&h->err, [&]() {
         reduced_local_inverse(*h->E, out, in, Ls_hat, iters, P);
         DWF_CUDA(cudaStreamSynchronize(h->E->st));

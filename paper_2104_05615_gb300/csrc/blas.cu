@@ -41,6 +41,12 @@ __device__ __forceinline__ void load_any(Prec p, const void *base, long nsite, l
 #pragma unroll
         for (int r = 0; r < 24; r++) v[r] = (R)t[r];
     } break;
+    case PFX16: {
+        float t[24];
+        load_sp<TFX16>(base, nsite, site, s, Ls, t);
+#pragma unroll
+        for (int r = 0; r < 24; r++) v[r] = (R)t[r];
+    } break;
     default: {
         float t[24];
         load_sp<TBF16>(base, nsite, site, s, Ls, t);
@@ -72,6 +78,12 @@ __device__ __forceinline__ void store_any(Prec p, void *base, long nsite, long s
 #pragma unroll
         for (int r = 0; r < 24; r++) t[r] = (float)v[r];
         store_sp<TF16>(base, nsite, site, s, Ls, t);
+    } break;
+    case PFX16: {
+        float t[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) t[r] = (float)v[r];
+        store_sp<TFX16>(base, nsite, site, s, Ls, t);
     } break;
     default: {
         float t[24];
@@ -367,7 +379,8 @@ __device__ __forceinline__ void load_canon(Prec p, const void *base, long Vh, lo
         const double *q = reinterpret_cast<const double *>(base) + off;
         for (int r = 0; r < 24; r++) v[r] = (R)q[r];
     } break;
-    case P32: {
+    case P32:
+    case PFX16: {  // fixed-point fields are exchanged as FP32
         const float *q = reinterpret_cast<const float *>(base) + off;
         for (int r = 0; r < 24; r++) v[r] = (R)q[r];
     } break;
@@ -391,7 +404,8 @@ __device__ __forceinline__ void store_canon(Prec p, void *base, long Vh, long cb
         double *q = reinterpret_cast<double *>(base) + off;
         for (int r = 0; r < 24; r++) q[r] = (double)v[r];
     } break;
-    case P32: {
+    case P32:
+    case PFX16: {
         float *q = reinterpret_cast<float *>(base) + off;
         for (int r = 0; r < 24; r++) q[r] = (float)v[r];
     } break;

@@ -27,6 +27,15 @@ struct TBF16 {
     static constexpr int NC = 3;
     static constexpr Prec P = PB16;
 };
+// 16-bit fixed point (Sec. 3.2): each real an int16, one FP32 scale per
+// colour-spinor (the 24 reals of a (site, s)); the stored scale is
+// max|v| / 32767, so value = integer * scale like the FP16 format
+struct TFX16 {
+    using R = float;
+    static constexpr int NC = 3;
+    static constexpr Prec P = PFX16;
+};
+constexpr float kFx16Max = 32767.f;
 
 template <class T>
 __device__ __forceinline__ const float *scale_ptr(const void *base, long nsite, int Ls)
@@ -116,6 +125,37 @@ __device__ __forceinline__ void load_sp<TBF16>(const void *base, long, long site
 #pragma unroll
     for (int c = 0; c < 3; c++) unpack8(__ldg(p + (size_t)c * Ls), v + 8 * c, __nv_bfloat16());
 }
+// eight int16 of a 16-byte chunk to floats
+__device__ __forceinline__ void unpack8_fx16(const uint4 &u, float *v)
+{
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        v[2 * i] = (float)(short)(w[i] & 0xffffu);
+        v[2 * i + 1] = (float)(short)(w[i] >> 16);
+    }
+}
+__device__ __forceinline__ uint4 pack8_fx16(const float *w)
+{
+    uint32_t q[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int lo = __float2int_rn(w[2 * i]), hi = __float2int_rn(w[2 * i + 1]);
+        q[i] = ((uint32_t)(unsigned short)(short)lo) | ((uint32_t)(unsigned short)(short)hi << 16);
+    }
+    return make_uint4(q[0], q[1], q[2], q[3]);
+}
+template <>
+__device__ __forceinline__ void load_sp<TFX16>(const void *base, long nsite, long site, int s,
+                                               int Ls, float *v)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(base) + (size_t)site * 3 * Ls + s;
+#pragma unroll
+    for (int c = 0; c < 3; c++) unpack8_fx16(__ldg(p + (size_t)c * Ls), v + 8 * c);
+    const float sc = __ldg(scale_ptr<TFX16>(base, nsite, Ls) + (size_t)site * Ls + s);
+#pragma unroll
+    for (int i = 0; i < 24; i++) v[i] *= sc;
+}
 template <>
 __device__ __forceinline__ void load_sp<TF16>(const void *base, long nsite, long site, int s,
                                               int Ls, float *v)
@@ -175,10 +215,44 @@ __device__ __forceinline__ void store_sp<TF16>(void *base, long nsite, long site
     scale_ptr<TF16>(base, nsite, Ls)[(size_t)site * Ls + s] = sc;
 }
 
-// FP16 store of v * f: the values are normalised by max|v| and the stored
-// scale is max|v| * f (the factor never touches the 24 values).
+// 16-bit fixed-point store of v with the stored scale multiplied by f
+__device__ __forceinline__ void store_fx16(void *base, long nsite, long site, int s, int Ls,
+                                           const float *v, float f)
+{
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
+    const float sc = m > 0.f ? m / kFx16Max : 1.f;
+    const float inv = m > 0.f ? kFx16Max / m : 0.f;
+    float w[24];
+#pragma unroll
+    for (int i = 0; i < 24; i++) w[i] = fminf(fmaxf(v[i] * inv, -kFx16Max), kFx16Max);
+    uint4 *p = reinterpret_cast<uint4 *>(base) + (size_t)site * 3 * Ls + s;
+#pragma unroll
+    for (int c = 0; c < 3; c++) p[(size_t)c * Ls] = pack8_fx16(w + 8 * c);
+    scale_ptr<TFX16>(base, nsite, Ls)[(size_t)site * Ls + s] = sc * f;
+}
+template <>
+__device__ __forceinline__ void store_sp<TFX16>(void *base, long nsite, long site, int s, int Ls,
+                                                const float *v)
+{
+    store_fx16(base, nsite, site, s, Ls, v, 1.f);
+}
+
+// Scaled 16-bit store of v * f (FP16 or 16-bit fixed point): the values are
+// normalised by max|v| and the factor goes into the stored scale only.
+template <class T>
 __device__ __forceinline__ void store_sp_scaled(void *base, long nsite, long site, int s, int Ls,
-                                                const float *v, float f)
+                                                const float *v, float f);
+template <>
+__device__ __forceinline__ void store_sp_scaled<TFX16>(void *base, long nsite, long site, int s, int Ls,
+                                                       const float *v, float f)
+{
+    store_fx16(base, nsite, site, s, Ls, v, f);
+}
+template <>
+__device__ __forceinline__ void store_sp_scaled<TF16>(void *base, long nsite, long site, int s, int Ls,
+                                                      const float *v, float f)
 {
     float m = 0.f;
 #pragma unroll
@@ -251,6 +325,11 @@ __device__ __forceinline__ void load_link12<TF16>(const void *links, long row, i
 }
 template <>
 __device__ __forceinline__ void load_link12<TBF16>(const void *links, long row, int k, float *u)
+{
+    load_link12_half(links, row, k, u);
+}
+template <>
+__device__ __forceinline__ void load_link12<TFX16>(const void *links, long row, int k, float *u)
 {
     load_link12_half(links, row, k, u);
 }

@@ -21,7 +21,9 @@
 
 namespace dwf {
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PFX16 = 4 };
+// formats stored with one FP32 scale per (site, s) after the data
+inline bool scaled_format(Prec p) { return p == P16 || p == PFX16; }
 
 constexpr int kSegPad = 32;  // every segment (block / system) is padded to this many sites
 
@@ -29,17 +31,17 @@ inline int elem_bytes(Prec p) { return p == P64 ? 8 : p == P32 ? 4 : 2; }
 inline size_t field_bytes(Prec p, long nsite, int Ls)
 {
     size_t b = (size_t)nsite * Ls * 24 * elem_bytes(p);
-    if (p == P16) b += (size_t)nsite * Ls * sizeof(float);
+    if (scaled_format(p)) b += (size_t)nsite * Ls * sizeof(float);
     return b;
 }
 // scale array of an FP16 field sits right after its data
 inline float *field_scale(void *data, Prec p, long nsite, int Ls)
 {
-    return p == P16 ? (float *)((char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
+    return scaled_format(p) ? (float *)((char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
 }
 inline const float *field_scale(const void *data, Prec p, long nsite, int Ls)
 {
-    return p == P16 ? (const float *)((const char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
+    return scaled_format(p) ? (const float *)((const char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
 }
 
 // One stage of an operator: out = Epilogue(F . hop(G . in)), see stage.cu.

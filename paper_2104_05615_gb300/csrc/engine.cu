@@ -451,7 +451,7 @@ static const void *matp(const Mats &m, MatKind k, Prec p)
     return p == P64 ? (const void *)m.d64[k] : (const void *)m.d32[k];
 }
 
-static bool is_half(Prec p) { return p == P16 || p == PB16; }
+static bool is_half(Prec p) { return p == P16 || p == PB16 || p == PFX16; }
 
 // Matrices of a stage: CUDA-core path F (and G), tensor-core path the fused
 // operand A; G is kept non-null on the tensor-core path only as a flag.

@@ -301,7 +301,7 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     // keep the solution increment in FP32 between reliable updates
     const Prec pacc = po == P64 ? P64 : P32;
     if (use_precond && (P.inner_prec == DWF_F64 || P.inner_iters < 0)) {
-        err = "inner precision must be FP32, FP16 or BF16 and k >= 0";
+        err = "inner precision must be FP32, FP16, BF16 or FX16 and k >= 0";
         return DWF_EINVAL;
     }
     if (P.use_reduced_ls && use_precond && (E.Ls_hat <= 0 || !E.Tm)) {

@@ -201,6 +201,9 @@ __device__ __forceinline__ void decode_chunks(const uint4 *p, int cs, typename T
             v[4 * c + 2] = f.z;
             v[4 * c + 3] = f.w;
         }
+    } else if constexpr (T::P == PFX16) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) unpack8_fx16(p[c * cs], v + 8 * c);
     } else if constexpr (T::P == P16) {
 #pragma unroll
         for (int c = 0; c < 3; c++) unpack8(p[c * cs], v + 8 * c, __half());
@@ -406,12 +409,12 @@ template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS, int TS
 // 16-bit stages with precomputed M_phi input are held to 64 registers (two
 // 512-thread blocks' worth per SM): the occupancy gain outweighs the extra
 // rematerialisation.  (M_phi on load needs more live values.)
-__global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi) ? 2 : 1)
+__global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == PFX16) && !kMphi) ? 2 : 1)
     stage_kernel(const StageArgs a)
 {
     using R = typename T::R;
-    constexpr bool kTC = (T::P == P16 || T::P == PB16);
-    constexpr bool kScale = (T::P == P16);
+    constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16);
+    constexpr bool kScale = (T::P == P16 || T::P == PFX16);
     constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
     constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
     constexpr int NC = T::NC;
@@ -692,7 +695,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
     // own aux column; the S2 tensor-core stage on FP16 storage keeps it as
     // stored (normalised half values and their scale, which is also their
     // max-abs) and feeds it to the operand tile in half2 arithmetic
-    constexpr bool kAuxRaw = kTC && kScale && !kTma && kMode == MODE_S2;
+    constexpr bool kAuxRaw = (T::P == P16) && !kTma && kMode == MODE_S2;
     R av[24];
 #pragma unroll
     for (int r = 0; r < 24; r++) av[r] = 0;
@@ -982,7 +985,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16) && !kMphi)
 
     if constexpr (kTC && kScale && kMode != MODE_S4) {
         // out holds D / (site scale): the factor goes into the stored scale
-        if (active) store_sp_scaled(a.out, a.nout, i, s, Ls, out, sMax[jl]);
+        if (active) store_sp_scaled<T>(a.out, a.nout, i, s, Ls, out, sMax[jl]);
     } else {
         if (active) store_sp<T>(a.out, a.nout, i, s, Ls, out);
     }
@@ -1026,13 +1029,13 @@ static void launch_t(const StageArgs &a, cudaStream_t st)
 {
     using R = typename T::R;
     using LE = typename LinkElem<T>::E;
-    constexpr bool kTC = (T::P == P16 || T::P == PB16);
+    constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16);
     constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
     constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
     const int TS = a.tile, Ls = a.Ls;
     const int nthr = (TS * Ls + 31) / 32 * 32;
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
-    const bool scale_bulk = (T::P == P16) && (Ls % 4 == 0);
+    const bool scale_bulk = (T::P == P16 || T::P == PFX16) && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, T::NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
                                    has_dot, !kTC || kMode == MODE_S4);
     static bool attr_set = false;

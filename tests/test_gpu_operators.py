@@ -1,7 +1,8 @@
 """GPU operator parity against the FP64 oracle, through the C ABI.
 
 Relative error ||out - out_oracle|| / ||out_oracle|| bounds (the accuracy each
-storage format allows): FP64 1e-12, FP32 1e-6, FP16/BF16 5e-3.
+storage format allows): FP64 1e-12, FP32 1e-6, FP16/BF16 and 16-bit fixed
+point 5e-3.
 """
 import numpy as np
 import pytest
@@ -10,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 from paper_2104_05615_gb300 import inputs  # noqa: E402
 
-TOL = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 5e-3}
+TOL = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 5e-3, "fx16": 5e-3}
 
 CASES = {
     # name: dims, Ls, sub, mass, eps, antiperiodic
@@ -39,7 +40,7 @@ def setup_case(orc, name):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "fx16"])
 def test_operator_parity(orc, name, prec):
     from paper_2104_05615_gb300.lattice import to_device, to_numpy
     lat, o, x, sub = setup_case(orc, name)
@@ -55,7 +56,7 @@ def test_operator_parity(orc, name, prec):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "fx16"])
 def test_pack_roundtrip(orc, prec):
     from paper_2104_05615_gb300.lattice import to_device, to_numpy
     lat, o, x, sub = setup_case(orc, "ragged_part")
@@ -64,8 +65,25 @@ def test_pack_roundtrip(orc, prec):
     back = lat.unpack(p, prec)
     if prec in ("f64", "f32"):
         assert torch.equal(back, xd)
+    elif prec == "fx16":
+        assert torch.equal(back.cpu(), fixed16_roundtrip(xd.cpu()))
     else:  # FP16 packs with one scale per colour-spinor
         assert relerr(to_numpy(back), to_numpy(xd)) < 2e-3
+
+
+def fixed16_roundtrip(x):
+    """The 16-bit fixed-point format of Sec. 3.2 written out in FP32: per
+    colour-spinor (24 reals) q = rint(v * (32767 / m)), m = max |v|, and the
+    value read back is q * (m / 32767) (m = 0: all zero)."""
+    v = torch.view_as_real(x).reshape(x.shape[0], x.shape[1], 24).numpy()
+    m = np.abs(v).max(axis=2, keepdims=True).astype(np.float32)
+    lim = np.float32(32767)
+    with np.errstate(divide="ignore"):
+        inv = np.where(m > 0, lim / m, np.float32(0)).astype(np.float32)
+    sc = np.where(m > 0, m / lim, np.float32(1)).astype(np.float32)
+    q = np.clip(np.rint((v * inv).astype(np.float32)), -lim, lim).astype(np.float32)
+    back = (q * sc).astype(np.float32).reshape(x.shape + (2,))
+    return torch.view_as_complex(torch.from_numpy(np.ascontiguousarray(back)))
 
 
 @pytest.mark.gpu

@@ -43,7 +43,7 @@ def test_mixed_cg_reliable_updates(orc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("inner", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("inner", ["f32", "f16", "bf16", "fx16"])
 def test_mspcg_converges_and_beats_cg(orc, inner):
     lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
     bd = torch.from_numpy(b).cuda()
@@ -177,7 +177,7 @@ def test_live_operator_timing(orc, graph):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("outer", ["f16", "bf16"])
+@pytest.mark.parametrize("outer", ["f16", "bf16", "fx16"])
 @pytest.mark.parametrize("mspcg", [True, False])
 def test_16bit_outer_iterations(orc, outer, mspcg):
     """16-bit outer vectors (Sec. 3.2: 16-bit outer iterations with FP64
