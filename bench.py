@@ -403,6 +403,8 @@ def main():
                     help="inner mode: inner storage formats (f32, f16, bf16, fx16)")
     ap.add_argument("--inner-ks", default="3,4,6,12,18", help="inner mode: inner iteration counts")
     ap.add_argument("--no-ablation", action="store_true", help="inner mode: skip the truncated-operator run")
+    ap.add_argument("--outer-prec", default=None,
+                    help="inner mode: outer vector format (f64, f32, f16, bf16, fx16; default the workload's)")
     ap.add_argument("--train-steps", type=int, default=8, help="train mode: descent steps")
     ap.add_argument("--train-mus", default=None,
                     help="train mode: comma-separated suppression factors mu (default: the workload's)")
@@ -524,6 +526,8 @@ def main():
                 p = solver_params(cfg, True)
                 p.inner_iters = k
                 p.inner_prec = PREC[pr]
+            if args.outer_prec:
+                p.outer_prec = PREC[args.outer_prec]
             fn = B.dwf_cg if k == "plain" else B.dwf_mspcg
             x = torch.zeros_like(bd)
             fn(lat.h, x, bd, p)
@@ -536,6 +540,7 @@ def main():
             e1.record()
             e1.synchronize()
             rows.append({"inner_iters": k, "inner_prec": pr, "truncated_local_op": bool(trunc),
+                         "outer_prec": args.outer_prec or cfg.get("outer_prec", "f32"),
                          "outer_iters": st.outer_iters,
                          "inner_iters_total": st.inner_iters_total, "reliable_updates": st.reliable_updates,
                          "seconds": e0.elapsed_time(e1) / 1000.0, "true_residual": st.true_residual})

@@ -125,24 +125,38 @@ __device__ __forceinline__ void load_sp<TBF16>(const void *base, long, long site
 #pragma unroll
     for (int c = 0; c < 3; c++) unpack8(__ldg(p + (size_t)c * Ls), v + 8 * c, __nv_bfloat16());
 }
-// eight int16 of a 16-byte chunk to floats
-__device__ __forceinline__ void unpack8_fx16(const uint4 &u, float *v)
+// eight int16 of a 16-byte chunk to floats, without the conversion unit:
+// with its sign bit flipped an int16 q reads as the unsigned q + 2^15, and
+// the float whose bits are 0x4B000000 | (q + 2^15) is 2^23 + 2^15 + q exactly
+constexpr float kFx16Bias = 8421376.f;  // 2^23 + 2^15
+// the biased values 2^23 + 2^15 + q (exact integers below 2^24)
+__device__ __forceinline__ void unpack8_fx16_biased(const uint4 &u, float *v)
 {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    const uint32_t w[4] = {u.x ^ 0x80008000u, u.y ^ 0x80008000u, u.z ^ 0x80008000u, u.w ^ 0x80008000u};
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        v[2 * i] = (float)(short)(w[i] & 0xffffu);
-        v[2 * i + 1] = (float)(short)(w[i] >> 16);
+        v[2 * i] = __uint_as_float(__byte_perm(w[i], 0x4B00u, 0x5410));
+        v[2 * i + 1] = __uint_as_float(__byte_perm(w[i], 0x4B00u, 0x5432));
     }
 }
-__device__ __forceinline__ uint4 pack8_fx16(const float *w)
+__device__ __forceinline__ void unpack8_fx16(const uint4 &u, float *v)
 {
+    unpack8_fx16_biased(u, v);
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] -= kFx16Bias;
+}
+// eight floats times inv, each product within +-32767 (to a few ulp),
+// rounded once to the nearest int16, ties to even: the fused v * inv +
+// 1.5 * 2^23 rounds at the units place and leaves the integer, in two's
+// complement, in the low 16 bits of the sum
+__device__ __forceinline__ uint4 pack8_fx16(const float *v, float inv)
+{
+    constexpr float kRound = 12582912.f;  // 1.5 * 2^23
     uint32_t q[4];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int lo = __float2int_rn(w[2 * i]), hi = __float2int_rn(w[2 * i + 1]);
-        q[i] = ((uint32_t)(unsigned short)(short)lo) | ((uint32_t)(unsigned short)(short)hi << 16);
-    }
+    for (int i = 0; i < 4; i++)
+        q[i] = __byte_perm(__float_as_uint(fmaf(v[2 * i], inv, kRound)),
+                           __float_as_uint(fmaf(v[2 * i + 1], inv, kRound)), 0x5410);
     return make_uint4(q[0], q[1], q[2], q[3]);
 }
 template <>
@@ -224,12 +238,11 @@ __device__ __forceinline__ void store_fx16(void *base, long nsite, long site, in
     for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
     const float sc = m > 0.f ? m / kFx16Max : 1.f;
     const float inv = m > 0.f ? kFx16Max / m : 0.f;
-    float w[24];
-#pragma unroll
-    for (int i = 0; i < 24; i++) w[i] = fminf(fmaxf(v[i] * inv, -kFx16Max), kFx16Max);
+    // q = rint(v * inv) with the product exact; |v| <= m, so |v * inv|
+    // exceeds 32767 by a few ulp at most and q stays within +-32767
     uint4 *p = reinterpret_cast<uint4 *>(base) + (size_t)site * 3 * Ls + s;
 #pragma unroll
-    for (int c = 0; c < 3; c++) p[(size_t)c * Ls] = pack8_fx16(w + 8 * c);
+    for (int c = 0; c < 3; c++) p[(size_t)c * Ls] = pack8_fx16(v + 8 * c, inv);
     scale_ptr<TFX16>(base, nsite, Ls)[(size_t)site * Ls + s] = sc * f;
 }
 template <>
@@ -460,10 +473,19 @@ namespace dwf {
 
 // Compile-time variants of the projector and the rebuild-and-accumulate step:
 // MU the direction, SG = +1 or -1 the sign in (1 + SG gamma_MU).  h is the
-// half spinor, already multiplied by the neighbour's weight.
-template <int MU, int SG, typename R>
+// half spinor, already multiplied by the neighbour's weight.  kBiased: p
+// holds 16-bit fixed-point integers q as the exact floats 2^23 + 2^15 + q
+// (unpack8_fx16_biased); a difference of two cancels the offset exactly and
+// a sum takes it off once, a + (b - 2 offset), each step exact (integers
+// below 2^24), so h is what the unbiased values give, with fewer operations.
+template <int MU, int SG, typename R, bool kBiased = false>
 __device__ __forceinline__ void project_ct(const R *p, R w, R *h)
 {
+    auto pl = [](R x, R y) {
+        if constexpr (kBiased) return x + (y - R(2 * kFx16Bias));
+        else return x + y;
+    };
+    auto mi = [](R x, R y) { return x - y; };
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const R p0r = p[(0 * 3 + c) * 2], p0i = p[(0 * 3 + c) * 2 + 1];
@@ -472,25 +494,25 @@ __device__ __forceinline__ void project_ct(const R *p, R w, R *h)
         const R p3r = p[(3 * 3 + c) * 2], p3i = p[(3 * 3 + c) * 2 + 1];
         R h0r, h0i, h1r, h1i;
         if constexpr (MU == 0) {  // h0 = p0 + SG i p3, h1 = p1 + SG i p2
-            h0r = SG > 0 ? p0r - p3i : p0r + p3i;
-            h0i = SG > 0 ? p0i + p3r : p0i - p3r;
-            h1r = SG > 0 ? p1r - p2i : p1r + p2i;
-            h1i = SG > 0 ? p1i + p2r : p1i - p2r;
+            h0r = SG > 0 ? mi(p0r, p3i) : pl(p0r, p3i);
+            h0i = SG > 0 ? pl(p0i, p3r) : mi(p0i, p3r);
+            h1r = SG > 0 ? mi(p1r, p2i) : pl(p1r, p2i);
+            h1i = SG > 0 ? pl(p1i, p2r) : mi(p1i, p2r);
         } else if constexpr (MU == 1) {  // h0 = p0 + SG p3, h1 = p1 - SG p2
-            h0r = SG > 0 ? p0r + p3r : p0r - p3r;
-            h0i = SG > 0 ? p0i + p3i : p0i - p3i;
-            h1r = SG > 0 ? p1r - p2r : p1r + p2r;
-            h1i = SG > 0 ? p1i - p2i : p1i + p2i;
+            h0r = SG > 0 ? pl(p0r, p3r) : mi(p0r, p3r);
+            h0i = SG > 0 ? pl(p0i, p3i) : mi(p0i, p3i);
+            h1r = SG > 0 ? mi(p1r, p2r) : pl(p1r, p2r);
+            h1i = SG > 0 ? mi(p1i, p2i) : pl(p1i, p2i);
         } else if constexpr (MU == 2) {  // h0 = p0 + SG i p2, h1 = p1 - SG i p3
-            h0r = SG > 0 ? p0r - p2i : p0r + p2i;
-            h0i = SG > 0 ? p0i + p2r : p0i - p2r;
-            h1r = SG > 0 ? p1r + p3i : p1r - p3i;
-            h1i = SG > 0 ? p1i - p3r : p1i + p3r;
+            h0r = SG > 0 ? mi(p0r, p2i) : pl(p0r, p2i);
+            h0i = SG > 0 ? pl(p0i, p2r) : mi(p0i, p2r);
+            h1r = SG > 0 ? pl(p1r, p3i) : mi(p1r, p3i);
+            h1i = SG > 0 ? mi(p1i, p3r) : pl(p1i, p3r);
         } else {  // h0 = p0 + SG p2, h1 = p1 + SG p3
-            h0r = SG > 0 ? p0r + p2r : p0r - p2r;
-            h0i = SG > 0 ? p0i + p2i : p0i - p2i;
-            h1r = SG > 0 ? p1r + p3r : p1r - p3r;
-            h1i = SG > 0 ? p1i + p3i : p1i - p3i;
+            h0r = SG > 0 ? pl(p0r, p2r) : mi(p0r, p2r);
+            h0i = SG > 0 ? pl(p0i, p2i) : mi(p0i, p2i);
+            h1r = SG > 0 ? pl(p1r, p3r) : mi(p1r, p3r);
+            h1i = SG > 0 ? pl(p1i, p3i) : mi(p1i, p3i);
         }
         h[(0 * 3 + c) * 2] = w * h0r;
         h[(0 * 3 + c) * 2 + 1] = w * h0i;

@@ -179,8 +179,9 @@ __device__ __forceinline__ void hop_dir_h2(const __half2 *p, const __half2 *U2, 
     accumulate_ct<MU, SG, float>(chi, acc);
 }
 
-// Decode the NC 16-byte chunks of one 5D spinor (stride `cs` chunks apart).
-template <class T>
+// Decode the NC 16-byte chunks of one 5D spinor (stride `cs` chunks apart);
+// kBiased: 16-bit fixed point left as the biased floats of unpack8_fx16_biased.
+template <class T, bool kBiased = false>
 __device__ __forceinline__ void decode_chunks(const uint4 *p, int cs, typename T::R *v)
 {
     if constexpr (T::P == P64) {
@@ -203,7 +204,10 @@ __device__ __forceinline__ void decode_chunks(const uint4 *p, int cs, typename T
         }
     } else if constexpr (T::P == PFX16) {
 #pragma unroll
-        for (int c = 0; c < 3; c++) unpack8_fx16(p[c * cs], v + 8 * c);
+        for (int c = 0; c < 3; c++) {
+            if constexpr (kBiased) unpack8_fx16_biased(p[c * cs], v + 8 * c);
+            else unpack8_fx16(p[c * cs], v + 8 * c);
+        }
     } else if constexpr (T::P == P16) {
 #pragma unroll
         for (int c = 0; c < 3; c++) unpack8(p[c * cs], v + 8 * c, __half());
@@ -603,6 +607,9 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             constexpr int k = decltype(kc)::value;
             constexpr int mu = k >> 1;
             constexpr int SG = ((k & 1) ? 1 : -1) * (kDag ? -1 : 1);
+            // fixed point: the projection takes the offset of the biased
+            // integers off itself (exactly), except where M_phi mixes slices
+            constexpr bool kFxB = (T::P == PFX16) && !kMphi;
             const int e = sN[jl * 8 + k];
             if (e == -1) return;
             const long idx = e >= 0 ? (long)e : (long)(-e - 2);
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             R sc = 1;
             if constexpr (kTma) {
                 const uint4 *cp = sCol + (size_t)(jl * 8 + k) * (colb / 16);
-                decode_chunks<T>(cp + s, Ls, psi);
+                decode_chunks<T, kFxB>(cp + s, Ls, psi);
                 if (kScale) {
                     sc = scale_bulk ? sScl[(jl * 8 + k) * Ls + s]
                                     : __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
@@ -653,7 +660,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
 #pragma unroll
                 for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + s);
                 if (kScale) sc = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
-                decode_chunks<T>(raw, 1, psi);
+                decode_chunks<T, kFxB>(raw, 1, psi);
                 if (kMphi) {
                     R q[24];
                     R s1 = 1, s2 = 1;
@@ -678,7 +685,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 }
             }
             R h[12], chi[12];
-            project_ct<mu, SG, R>(psi, e >= 0 ? sc : -sc, h);
+            project_ct<mu, SG, R, kFxB>(psi, e >= 0 ? sc : -sc, h);
             su3_mul_half_smem<R>(sU + (jl * 8 + k) * kLinkStride, h, chi);
             accumulate_ct<mu, SG, R>(chi, acc);
         };

@@ -72,16 +72,19 @@ def test_pack_roundtrip(orc, prec):
 
 
 def fixed16_roundtrip(x):
-    """The 16-bit fixed-point format of Sec. 3.2 written out in FP32: per
-    colour-spinor (24 reals) q = rint(v * (32767 / m)), m = max |v|, and the
-    value read back is q * (m / 32767) (m = 0: all zero)."""
+    """The 16-bit fixed-point format of Sec. 3.2 written out: per
+    colour-spinor (24 FP32 reals) m = max |v|, inv = 32767 / m in FP32,
+    q = rint(v * inv) of the exact product (ties to even), and the value read
+    back is q * (m / 32767) in FP32 (m = 0: all zero)."""
     v = torch.view_as_real(x).reshape(x.shape[0], x.shape[1], 24).numpy()
     m = np.abs(v).max(axis=2, keepdims=True).astype(np.float32)
     lim = np.float32(32767)
     with np.errstate(divide="ignore"):
         inv = np.where(m > 0, lim / m, np.float32(0)).astype(np.float32)
     sc = np.where(m > 0, m / lim, np.float32(1)).astype(np.float32)
-    q = np.clip(np.rint((v * inv).astype(np.float32)), -lim, lim).astype(np.float32)
+    q = np.rint(v.astype(np.float64) * inv.astype(np.float64))  # FP32 x FP32 is exact in FP64
+    assert np.abs(q).max() <= 32767
+    q = q.astype(np.float32)
     back = (q * sc).astype(np.float32).reshape(x.shape + (2,))
     return torch.view_as_complex(torch.from_numpy(np.ascontiguousarray(back)))
 
