@@ -198,7 +198,7 @@ dwf_status dwf_set_reduced_ls(dwf_handle *h, int Ls_hat, const double *T_host, d
  *
  * dwf_reduced_local_inverse: out = CG_iters(Mhat) in, x0 = 0, every block
  * independently (the inner solve of the preconditioner run to `iters`
- * iterations, standing in for Mhat^-1); p->inner_prec (FP32, FP16 or BF16;
+ * iterations, standing in for Mhat^-1); p->inner_prec (FP32, FP16, BF16 or FX16;
  * the 16-bit formats need Ls_hat <= 16) sets the inner storage, p null means
  * dwf_default_params.  in, out: Ls_hat slices, out != in.
  *
