@@ -397,6 +397,8 @@ def main():
     ap.add_argument("--op-reps", type=int, default=3)
     ap.add_argument("--kcfg", default=None,
                     help="fixed stage launch config 'tile,gather' for both operators (ops and solve modes)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="ops mode: also time the FP64 D^+D and measure the CUDA-core FMA rates")
     ap.add_argument("--op-precs", default=None,
                     help="ops mode: also time the local operator in these storage formats")
     ap.add_argument("--inner-precs", default="f16,bf16",
@@ -454,6 +456,12 @@ def main():
         extra = {}
         for pr in (args.op_precs.split(",") if args.op_precs else []):
             extra[f"local_ms_{pr}"] = time_op(lat, B.DWF_OP_LOCAL_DDAGD, pr, args.op_reps, flush) * 1e3
+        if args.peaks:
+            # the FP64 operator of the reliable updates against the measured
+            # FP64 FMA rate (the FP32 rate for context)
+            extra["global_ms_f64"] = time_op(lat, B.DWF_OP_DDAGD, "f64", args.op_reps, flush) * 1e3
+            extra["fma_peak_tflops"] = {"f32": B.dwf_fma_peak(lat.h, B.DWF_F32),
+                                        "f64": B.dwf_fma_peak(lat.h, B.DWF_F64)}
         if rank == 0:
             print(json.dumps({"local_ms": tl * 1e3, "global_ms": tg * 1e3, **extra}))
         return

@@ -287,6 +287,16 @@ dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
 /* Kernel launches issued by this library since load (process-wide). */
 long long dwf_kernel_launch_count(void);
 
+/* Measured fused multiply-add rate of the CUDA cores of the handle's device,
+ * the compute roof of the FP32 stages and of the FP64 operator used by the
+ * reliable updates (the roofline model of Sec. 3.1.1 needs the device's
+ * peak rate).  prec: DWF_F32 or DWF_F64 (else DWF_EINVAL).  Runs one full
+ * wave of independent FMA chains on the handle's stream (a warm-up and three
+ * timed launches, a few ms each for FP32, ~15 ms for FP64), synchronises, and
+ * writes the best rate in TFLOP/s (2 flops per FMA) to *tflops_host.
+ * DWF_ECUDA on a CUDA error (dwf_last_error gives it). */
+dwf_status dwf_fma_peak(dwf_handle *h, dwf_prec prec, double *tflops_host);
+
 #ifdef __cplusplus
 }
 #endif

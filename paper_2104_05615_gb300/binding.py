@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
             "dwf_apply_packed_static": (i, [vp, vp, vp, i, i, vp]),
             "dwf_get_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
             "dwf_set_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
+            "dwf_fma_peak": (i, [vp, i, C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -308,3 +309,10 @@ def dwf_set_kernel_config(h, prec, op_kind, tile_sites, gather):
 
 def dwf_kernel_launch_count():
     return lib().dwf_kernel_launch_count()
+
+
+def dwf_fma_peak(h, prec):
+    """Measured CUDA-core FMA rate (TFLOP/s) in DWF_F32 or DWF_F64."""
+    v = C.c_double()
+    check(lib().dwf_fma_peak(h, int(prec), C.byref(v)), h)
+    return v.value

@@ -181,3 +181,18 @@ def test_kernel_config_validation(orc):
     c = B.dwf_kernel_config()
     B.check(B.lib().dwf_get_kernel_config(lat.h, B.DWF_F32, 0, B.C.byref(c)), lat.h)
     assert (c.tile_sites, c.gather) == (8, 0)
+
+
+@pytest.mark.gpu
+def test_fma_peak_measured(orc):
+    """dwf_fma_peak: a plausible FP32 and FP64 FMA rate, FP64 below FP32, and
+    storage formats without CUDA-core arithmetic of their own rejected."""
+    from paper_2104_05615_gb300 import binding as B
+    lat, o, x, sub = setup_case(orc, "ragged")
+    f32 = B.dwf_fma_peak(lat.h, B.DWF_F32)
+    f64 = B.dwf_fma_peak(lat.h, B.DWF_F64)
+    assert 1.0 < f32 < 1000.0
+    assert 0.01 < f64 < f32
+    for bad in (B.DWF_F16, B.DWF_BF16, B.DWF_FX16, 7):
+        with pytest.raises(B.DwfError):
+            B.dwf_fma_peak(lat.h, bad)
