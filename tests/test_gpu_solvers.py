@@ -84,17 +84,19 @@ def test_reduced_ls_preconditioner_matches_oracle(orc):
 
 
 @pytest.mark.gpu
-def test_mspcg_reduced_ls_converges(orc):
+@pytest.mark.parametrize("inner", ["bf16", "fx16"])
+def test_mspcg_reduced_ls_converges(orc, inner):
     from paper_2104_05615_gb300.lattice import heuristic_T
     lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
     lat.set_reduced_ls(4, heuristic_T(8, 4), 0.85)
-    x, st = lat.solve(torch.from_numpy(b).cuda(), mspcg=True, tol=1e-10, inner_prec="bf16",
+    x, st = lat.solve(torch.from_numpy(b).cuda(), mspcg=True, tol=1e-10, inner_prec=inner,
                       use_reduced_ls=1)
     assert o.true_residual(x.cpu().numpy(), b) <= 1e-10 * 1.01
 
 
 @pytest.mark.gpu
-def test_batched_mspcg_uneven_systems(orc):
+@pytest.mark.parametrize("inner", ["f16", "fx16"])
+def test_batched_mspcg_uneven_systems(orc, inner):
     """Independent lattices of different sizes and masses in one batch; each
     system's answer verified by its own oracle."""
     from paper_2104_05615_gb300 import binding as B
@@ -111,7 +113,8 @@ def test_batched_mspcg_uneven_systems(orc):
     bt = B.dwf_batch_create([l.h for l in lats])
     try:
         bd = [torch.from_numpy(b).cuda() for b in bs]
-        tot, per = B.dwf_batch_mspcg(bt, xs, bd, B.default_params(tol=1e-9, inner_prec=B.DWF_F16))
+        from paper_2104_05615_gb300.lattice import PREC
+        tot, per = B.dwf_batch_mspcg(bt, xs, bd, B.default_params(tol=1e-9, inner_prec=PREC[inner]))
         assert tot.converged
         for k in range(3):
             assert oracles[k].true_residual(xs[k].cpu().numpy(), bs[k]) <= 1e-9 * 1.01
