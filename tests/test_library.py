@@ -48,3 +48,62 @@ def test_oracle_library_builds_and_loads():
     import oracle
     path = oracle.build()
     ctypes.CDLL(path, mode=ctypes.RTLD_LOCAL | os.RTLD_NOW)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "dwf.h"
+
+static int fail(const char *what) { fprintf(stderr, "%s\n", what); return 1; }
+
+int main(void)
+{
+    dwf_solver_params p;
+    dwf_handle *h = NULL;
+    double g[2 * 4 * 9 * 2] = {0};
+    const int odd[4] = {3, 4, 4, 4}, sub[4] = {4, 4, 4, 4};
+    double t = 0.0;
+    dwf_default_params(&p);
+    if (p.tol != 1e-10 || p.inner_iters != 6 || p.inner_prec != DWF_F16 || p.outer_prec != DWF_F32)
+        return fail("default parameters");
+    if (!dwf_status_string(DWF_EINVAL) || !strlen(dwf_status_string(DWF_EINVAL)))
+        return fail("status string");
+    /* argument checks that come before any device work */
+    if (dwf_create(&h, NULL, sub, 8, 1.5, 0.5, 1.8, 0.1, NULL, 0, NULL) != DWF_EINVAL || h)
+        return fail("null gauge accepted");
+    if (dwf_create(&h, g, odd, 8, 1.5, 0.5, 1.8, 0.1, NULL, 0, NULL) != DWF_EINVAL || h)
+        return fail("odd extent accepted");
+    if (dwf_create(&h, g, sub, 0, 1.5, 0.5, 1.8, 0.1, NULL, 0, NULL) != DWF_EINVAL || h)
+        return fail("Ls = 0 accepted");
+    if (dwf_fma_peak(NULL, DWF_F32, &t) != DWF_EINVAL) return fail("null handle accepted");
+    if (strcmp(dwf_last_error(NULL), "null handle") != 0) return fail("last error of null");
+    if (dwf_kernel_launch_count() != 0) return fail("launches without a device call");
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_a_c_client_links(tmp_path):
+    """include/dwf.h compiles as strict C99 (no C++ in the ABI), a C program
+    links against the library and its host-side calls behave as documented."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2104_05615_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_path = build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    lib_dir = os.path.dirname(lib_path)
+    cmd = [cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror",
+           "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+           "-L" + lib_dir, "-ldwf_gb300", "-Wl,-rpath," + lib_dir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
