@@ -401,6 +401,34 @@ def test_reduced_ls_operator_hermitian(orc):
     assert abs(np.vdot(y, o.T_apply(T, x, Lsh)) - np.vdot(o.T_apply(T, y, Lsh, True), x)) < 1e-10
 
 
+def test_T_apply_selection_is_indexing(orc):
+    """T indexed (s, spin) x (t, spin') (Sec. 3.3: T acts on spin x fifth
+    dimension, trivially on colour and sites).  A T that picks slice sel[s]
+    and spin perm[a] for output (s, a) must reduce to array indexing, and T^+
+    to the matching scatter; a transposed or reordered (s, spin) index fails."""
+    dims, Ls, Lsh = (2, 2, 2, 2), 6, 3
+    o, _ = make(orc, dims, Ls)
+    sel, perm = [4, 0, 2], [2, 0, 3, 1]
+    T = np.zeros((4 * Lsh, 4 * Ls), dtype=np.complex128)
+    for s in range(Lsh):
+        for a in range(4):
+            T[s * 4 + a, sel[s] * 4 + perm[a]] = 1.0
+    x = rnd(o.cb_shape(), 5)
+    y = o.T_apply(T, x, Lsh)
+    np.testing.assert_array_equal(y, x[sel][:, :, perm, :])
+    back = o.T_apply(T, y, Lsh, dagger=True)
+    want = np.zeros_like(x)
+    for s in range(Lsh):
+        want[sel[s]][:, perm, :] = y[s]
+    np.testing.assert_array_equal(back, want)
+    # a complex phase per row is conjugated by the adjoint
+    ph = np.exp(1j * np.arange(4 * Lsh))
+    y2 = o.T_apply(ph[:, None] * T, x, Lsh)
+    np.testing.assert_allclose(y2, y * ph.reshape(Lsh, 1, 4, 1), rtol=0, atol=1e-15)
+    back2 = o.T_apply(ph[:, None] * T, y2, Lsh, dagger=True)
+    np.testing.assert_allclose(back2, want, rtol=0, atol=1e-14)
+
+
 def test_mspcg_reduces_outer_iterations(orc):
     """Qualitative (Sec. 2.5): with 6 inner iterations the outer count drops."""
     dims, Ls, sub = (8, 4, 4, 4), 4, (4, 4, 4, 4)
