@@ -330,6 +330,22 @@ def _textbook_pcg(A, b, Minv, tol, maxit, pr=False):
     return x, np.array(hist)
 
 
+def test_true_residual_is_the_relative_residual(orc):
+    """The residual every GPU solve is judged by: ||b - D^+D x|| / ||b|| in
+    FP64, against the dense matrix (assembled column by column) and numpy's
+    norms; 1 at x = 0, rounding level at the dense LU solution."""
+    o, _ = make(orc, (2, 2, 2, 2), 4, mass=0.1)
+    A = dense_of(o.DdagD, o.cb_shape())
+    b, x = rnd(o.cb_shape(), 21), rnd(o.cb_shape(), 22)
+    assert abs(o.true_residual(np.zeros_like(b), b) - 1.0) < 1e-15
+    want = np.linalg.norm(b.reshape(-1) - A @ x.reshape(-1)) / np.linalg.norm(b)
+    assert abs(o.true_residual(x, b) - want) <= 1e-12 * want
+    xs = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
+    assert o.true_residual(xs, b) < 1e-12
+    assert abs(o.true_residual(xs + 1e-3 * x, b) - 1e-3 * np.linalg.norm(A @ x.reshape(-1))
+               / np.linalg.norm(b)) < 1e-9
+
+
 def test_cg_matches_textbook_and_converges(orc):
     dims, Ls = (2, 2, 2, 4), 4
     o, _ = make(orc, dims, Ls, mass=0.05)
