@@ -381,6 +381,41 @@ def test_mspcg_exact_block_inverse_is_block_jacobi_pcg(orc):
     np.testing.assert_allclose(res["history"][:6], h_tb[:6], rtol=1e-5)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_preconditioner_is_k_steps_of_block_cg(orc, k):
+    """z = M^-1 r of Sec. 2.4/2.5: on every block, exactly k CG iterations from
+    a zero guess on the block's principal submatrix of D^+D.  k steps of CG
+    from zero give the unique A-norm minimiser over the k-dimensional Krylov
+    space, so a textbook CG on the dense blocks fixes the result."""
+    dims, Ls, sub = (8, 2, 2, 2), 2, (4, 2, 2, 2)
+    o, _ = make(orc, dims, Ls, mass=0.1)
+    A = dense_of(o.DdagD, o.cb_shape())
+    r = rnd(o.cb_shape(), 9)
+    bid, nb = o.block_ids(sub)
+    z_tb = np.zeros(r.size, dtype=np.complex128)
+    rv = r.reshape(-1)
+    for blk in range(nb):
+        m = np.kron(np.ones(Ls), np.repeat(bid == blk, 12)).astype(bool)
+        As, bs = A[np.ix_(m, m)], rv[m]
+        x, res, p = np.zeros_like(bs), bs.copy(), bs.copy()
+        rr = np.vdot(res, res).real
+        for _ in range(k):
+            Ap = As @ p
+            al = rr / np.vdot(p, Ap).real
+            x, res = x + al * p, res - al * Ap
+            rr_new = np.vdot(res, res).real
+            p, rr = res + (rr_new / rr) * p, rr_new
+        z_tb[m] = x
+    z = o.precond(r, orc.PREC_MSPCG, k=k, sub=sub)
+    np.testing.assert_allclose(z.reshape(-1), z_tb, rtol=0, atol=1e-11 * np.abs(z_tb).max())
+    if k < 5:  # not yet the exact block solve
+        z_exact = np.zeros_like(z_tb)
+        for blk in range(nb):
+            m = np.kron(np.ones(Ls), np.repeat(bid == blk, 12)).astype(bool)
+            z_exact[m] = np.linalg.solve(A[np.ix_(m, m)], rv[m])
+        assert np.linalg.norm(z_tb - z_exact) > 1e-6 * np.linalg.norm(z_exact)
+
+
 def test_identity_preconditioner_reproduces_cg(orc):
     """Reduced-Ls form with Ls_hat = Ls, T = 1 and mu = 0 is the plain MSPCG
     preconditioner; with the identity (no preconditioner) PCG+FR is CG."""
