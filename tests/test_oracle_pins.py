@@ -430,6 +430,22 @@ def test_identity_preconditioner_reproduces_cg(orc):
     np.testing.assert_allclose(z3, z1 + 0.3 * r, atol=1e-13)
 
 
+def test_reduced_preconditioner_composes_its_pinned_parts(orc):
+    """Sec. 3.3: z = T^+ (k CG steps on Mhat) T r + mu r, with Mhat the local
+    operator at Ls_hat; composed here from the separately pinned T map and the
+    k-step block CG at Ls_hat, for a random complex T."""
+    dims, Ls, Lsh, sub, k = (8, 2, 2, 2), 4, 2, (4, 2, 2, 2), 3
+    o, _ = make(orc, dims, Ls, mass=0.1)
+    oh = o.with_Ls(Lsh)
+    rng = np.random.default_rng(12)
+    T = rng.standard_normal((4 * Lsh, 4 * Ls)) + 1j * rng.standard_normal((4 * Lsh, 4 * Ls))
+    r = rnd(o.cb_shape(), 13)
+    want = o.T_apply(T, oh.precond(o.T_apply(T, r, Lsh), orc.PREC_MSPCG, k=k, sub=sub), Lsh,
+                     dagger=True) + 0.4 * r
+    got = o.precond(r, orc.PREC_REDUCED, k=k, sub=sub, Ls_hat=Lsh, T=T, mu=0.4)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
 def test_reduced_ls_operator_hermitian(orc):
     """T^+ Mhat^-1 T is Hermitian and rank deficient for Ls_hat < Ls (Sec. 3.3)."""
     dims, Ls, Lsh, sub = (2, 2, 2, 2), 4, 2, (2, 2, 2, 2)
