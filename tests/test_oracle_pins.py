@@ -331,7 +331,7 @@ def _textbook_pcg(A, b, Minv, tol, maxit, pr=False):
 
 
 def test_true_residual_is_the_relative_residual(orc):
-    """The residual every GPU solve is judged by: ||b - D^+D x|| / ||b|| in
+    """The residual every GPU solve test is decided by: ||b - D^+D x|| / ||b|| in
     FP64, against the dense matrix (assembled column by column) and numpy's
     norms; 1 at x = 0, rounding level at the dense LU solution."""
     o, _ = make(orc, (2, 2, 2, 2), 4, mass=0.1)
