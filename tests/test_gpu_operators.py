@@ -196,3 +196,32 @@ def test_fma_peak_measured(orc):
     for bad in (B.DWF_F16, B.DWF_BF16, B.DWF_FX16, 7):
         with pytest.raises(B.DwfError):
             B.dwf_fma_peak(lat.h, bad)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "fx16"])
+def test_every_kernel_config_matches_oracle(orc, prec):
+    """Every launch shape the autotuner may pick (site tile x direct or
+    bulk-copy neighbour gather) gives the global D^+D and the local operator
+    within the format's tolerance; shapes that do not fit are refused."""
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import PREC, to_device, to_numpy
+    lat, o, x, sub = setup_case(orc, "ls12")
+    xd = to_device(x, prec)
+    xin = to_numpy(xd)
+    want = {"DdagD": o.DdagD(xin), "local": o.local_DdagD(xin, sub)}
+    ran = set()
+    for gather in (0, 1):
+        for tile in (4, 8, 16, 32):
+            for kind, op in ((0, "DdagD"), (1, "local")):
+                try:
+                    B.dwf_set_kernel_config(lat.h, PREC[prec], kind, tile, gather)
+                except B.DwfError as err:
+                    assert err.status == B.DWF_EINVAL
+                    continue
+                e = relerr(to_numpy(lat.apply(op, xd, prec)), want[op])
+                assert e < TOL[prec], f"{prec} {op} tile {tile} gather {gather}: {e:.3e}"
+                ran.add((op, gather))
+    assert {("DdagD", 0), ("local", 0)} <= ran
+    if prec != "f64":
+        assert {("DdagD", 1), ("local", 1)} <= ran
