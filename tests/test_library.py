@@ -76,6 +76,18 @@ int main(void)
         return fail("odd extent accepted");
     if (dwf_create(&h, g, sub, 0, 1.5, 0.5, 1.8, 0.1, NULL, 0, NULL) != DWF_EINVAL || h)
         return fail("Ls = 0 accepted");
+    {
+        /* a partitioned extent needs lattice - block >= 4 (the snake halo),
+           blocks must divide the lattice and be even */
+        const int dims[4] = {8, 4, 4, 4};
+        const int narrow[4] = {6, 4, 4, 4}, ragged[4] = {3, 4, 4, 4}, odd_blk[4] = {4, 4, 4, 2};
+        if (dwf_create(&h, g, dims, 4, 1.5, 0.5, 1.8, 0.1, narrow, 0, NULL) != DWF_EINVAL || h)
+            return fail("block that does not divide accepted");
+        if (dwf_create(&h, g, dims, 4, 1.5, 0.5, 1.8, 0.1, ragged, 0, NULL) != DWF_EINVAL || h)
+            return fail("odd block accepted");
+        if (dwf_create(&h, g, dims, 4, 1.5, 0.5, 1.8, 0.1, odd_blk, 0, NULL) != DWF_EINVAL || h)
+            return fail("block too large for the snake halo accepted");
+    }
     if (dwf_fma_peak(NULL, DWF_F32, &t) != DWF_EINVAL) return fail("null handle accepted");
     if (strcmp(dwf_last_error(NULL), "null handle") != 0) return fail("last error of null");
     if (dwf_kernel_launch_count() != 0) return fail("launches without a device call");
