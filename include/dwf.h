@@ -148,6 +148,12 @@ typedef struct {
     long long e2_sites, e2_sites_padded;
 } dwf_geometry;
 dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g);
+/* The same counts for a lattice and block dims (same rules as dwf_create;
+ * subdomain NULL = unpartitioned) without creating a handle or touching a
+ * device: host-only, for sizing memory before dwf_create.  DWF_EINVAL for
+ * dims or blocks dwf_create would refuse, DWF_EUNSUPPORTED for more than
+ * 65535 blocks. */
+dwf_status dwf_query_geometry(const int dims[4], const int subdomain[4], dwf_geometry *g);
 
 /* Canonical <-> packed layout conversion on device buffers (stream 0 =
  * handle's stream).  Same precision on both sides. */

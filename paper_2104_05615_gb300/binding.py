@@ -98,6 +98,7 @@ def lib() -> C.CDLL:
             "dwf_get_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
             "dwf_set_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
             "dwf_fma_peak": (i, [vp, i, C.POINTER(C.c_double)]),
+            "dwf_query_geometry": (i, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(dwf_geometry)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -289,6 +290,15 @@ def dwf_batch_mspcg(bt, xs, bs, params=None):
 def dwf_get_geometry(h):
     g = dwf_geometry()
     check(lib().dwf_get_geometry(h, C.byref(g)), h)
+    return g.as_dict()
+
+
+def dwf_query_geometry(dims, sub=None):
+    """Site counts of a lattice and block dims without a handle or a device."""
+    g = dwf_geometry()
+    d = (C.c_int * 4)(*[int(v) for v in dims])
+    sb = (C.c_int * 4)(*[int(v) for v in sub]) if sub is not None else None
+    check(lib().dwf_query_geometry(d, sb, C.byref(g)))
     return g.as_dict()
 
 

@@ -146,10 +146,8 @@ size_t dwf_packed_bytes(const dwf_handle *h, dwf_prec prec, int Ls)
     return field_bytes((Prec)prec, h->E->ne, Ls > 0 ? Ls : h->Ls);
 }
 
-dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g)
+static void fill_geometry(const LatticeGeom &G, dwf_geometry *g)
 {
-    if (!h || !g) return DWF_EINVAL;
-    const LatticeGeom &G = h->g;
     g->even_sites = G.Vh;
     g->even_sites_padded = G.ne();
     g->blocks = G.nblk;
@@ -159,6 +157,27 @@ dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g)
     g->o1_sites_padded = G.O1_pad;
     g->e2_sites = G.E2 - (G.Nb_pad - G.Nb);
     g->e2_sites_padded = G.E2_pad;
+}
+
+dwf_status dwf_get_geometry(const dwf_handle *h, dwf_geometry *g)
+{
+    if (!h || !g) return DWF_EINVAL;
+    fill_geometry(h->g, g);
+    return DWF_OK;
+}
+
+dwf_status dwf_query_geometry(const int dims[4], const int subdomain[4], dwf_geometry *g)
+{
+    if (!dims || !g) return DWF_EINVAL;
+    try {
+        LatticeGeom G;
+        std::string err;
+        if (!build_geometry(G, dims, subdomain, 0, err)) return DWF_EINVAL;
+        if (G.nblk > 65535) return DWF_EUNSUPPORTED;
+        fill_geometry(G, g);
+    } catch (...) {
+        return DWF_ENOMEM;
+    }
     return DWF_OK;
 }
 

@@ -119,3 +119,51 @@ def test_header_is_plain_c_and_a_c_client_links(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
+
+
+def _brute_regions(dims, sub):
+    """Per block (the one at the origin): even interior sites, odd sites within
+    L1 distance 1 and even sites within L1 distance 2 of it, counted over the
+    whole periodic lattice (the block is a box, so the distance is the sum of
+    the per-dimension distances to its interval)."""
+    import numpy as np
+    grids = np.meshgrid(*[np.arange(L) for L in dims], indexing="ij")
+    dist = np.zeros(dims, dtype=np.int64)
+    for mu, (L, S) in enumerate(zip(dims, sub)):
+        y = grids[mu]
+        if S == L:
+            continue
+        inside = y < S
+        d = np.minimum((y - (S - 1)) % L, (-y) % L)
+        dist += np.where(inside, 0, d)
+    par = sum(grids) % 2
+    return (int(((dist == 0) & (par == 0)).sum()), int(((dist <= 1) & (par == 1)).sum()),
+            int(((dist <= 2) & (par == 0)).sum()))
+
+
+def test_query_geometry_regions_match_brute_force():
+    """dwf_query_geometry (host-only) against a brute-force count of the
+    snake-term regions (Sec. 2.3 / 3.1.2): the even interior, the odd sites
+    one hop out and the even sites two hops out, for the workloads' block
+    shapes; refused shapes give DWF_EINVAL."""
+    import numpy as np
+    import pytest
+    from paper_2104_05615_gb300 import binding as B
+    cases = [((16, 16, 16, 32), (8, 8, 8, 8)), ((32, 32, 32, 64), (16, 16, 16, 16)),
+             ((8, 8, 8, 8), (4, 4, 4, 4)), ((12, 12, 12, 12), (4, 4, 4, 4)),
+             ((8, 8, 8, 16), (4, 4, 4, 4)), ((8, 4, 4, 4), (4, 4, 4, 4)),
+             ((12, 2, 2, 2), (6, 2, 2, 2)), ((6, 2, 2, 2), (6, 2, 2, 2))]
+    for dims, sub in cases:
+        g = B.dwf_query_geometry(dims, sub)
+        interior, o1, e2 = _brute_regions(dims, sub)
+        nblk = int(np.prod(dims) // np.prod(sub))
+        assert g["blocks"] == nblk and g["even_sites"] == np.prod(dims) // 2, (dims, sub)
+        assert (g["block_sites"], g["o1_sites"], g["e2_sites"]) == (interior, o1, e2), (dims, sub, g)
+        for k in ("block_sites", "o1_sites", "e2_sites"):
+            assert g[k + "_padded"] >= g[k] and g[k + "_padded"] % 32 == 0, (dims, sub, k)
+    assert B.dwf_query_geometry((6, 2, 2, 2)) == B.dwf_query_geometry((6, 2, 2, 2), (6, 2, 2, 2))
+    for dims, sub in (((4, 4, 4, 4), (2, 4, 4, 4)), ((8, 4, 4, 4), (6, 4, 4, 4)),
+                      ((3, 4, 4, 4), None), ((8, 4, 4, 4), (4, 4, 4, 3))):
+        with pytest.raises(B.DwfError) as e:
+            B.dwf_query_geometry(dims, sub)
+        assert e.value.status == B.DWF_EINVAL
