@@ -8,6 +8,7 @@
 // work to hide the FMA latency at full occupancy), unrolled so the loop
 // control costs a few percent of the issue slots; one FMA = 2 flops.
 #include <cfloat>
+#include <new>
 
 #include "engine.h"
 
@@ -91,10 +92,13 @@ extern "C" dwf_status dwf_fma_peak(dwf_handle *h, dwf_prec prec, double *tflops)
         *tflops = prec == DWF_F32 ? measure<float>(E, 1 << 16) : measure<double>(E, 1 << 12);
     } catch (const CudaError &e) {
         dwf_handle_set_error(h, cudaGetErrorString(e.err));
-        return DWF_ECUDA;
+        return e.err == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
+    } catch (const std::bad_alloc &) {
+        dwf_handle_set_error(h, "host allocation failed");
+        return DWF_ENOMEM;
     } catch (const std::exception &e) {
         dwf_handle_set_error(h, e.what());
-        return DWF_ENOMEM;
+        return DWF_ECUDA;
     }
     return DWF_OK;
 }

@@ -87,7 +87,7 @@ extern "C" dwf_status dwf_apply_packed_static(dwf_handle *h, void *out, const vo
         E.st = old;
     } catch (const CudaError &e) {
         dwf_handle_set_error(h, cudaGetErrorString(e.err));
-        return DWF_ECUDA;
+        return e.err == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
     } catch (const std::exception &e) {
         dwf_handle_set_error(h, e.what());
         return DWF_EINVAL;
