@@ -512,9 +512,7 @@ void Engine::autotune(Prec p, int which, int Ls_op, int reps)
     void *y = ws("tune_y", field_bytes(p, n, Ls_op));
     // finite, normal values in every storage format (and in the FP16 scales)
     DWF_CUDA(cudaMemsetAsync(x, 0x3c, field_bytes(p, n, Ls_op), st));
-    cudaEvent_t e0, e1;
-    DWF_CUDA(cudaEventCreate(&e0));
-    DWF_CUDA(cudaEventCreate(&e1));
+    EventPair ev;
     std::vector<KCfg> cand;
     const int tiles[] = {4, 8, 16, 32};
     for (int gather = 0; gather < (p == P64 ? 1 : 2); gather++)
@@ -529,23 +527,30 @@ void Engine::autotune(Prec p, int which, int Ls_op, int reps)
     // two rounds over the candidates, each kept at its faster round (one
     // noisy measurement must not decide)
     std::vector<float> tbest(cand.size(), 1e30f);
-    for (int round = 0; round < 2; round++)
-        for (size_t q = 0; q < cand.size(); q++) {
-            c.tile = cand[q].tile;
-            c.gather = cand[q].gather;
-            auto run = [&]() {
-                if (which == 0) apply_global(p, DWF_OP_DDAGD, y, x, nullptr);
-                else apply_local(p, Ls_op, y, x, nullptr);
-            };
-            run();
-            DWF_CUDA(cudaEventRecord(e0, st));
-            for (int r = 0; r < reps; r++) run();
-            DWF_CUDA(cudaEventRecord(e1, st));
-            DWF_CUDA(cudaEventSynchronize(e1));
-            float ms = 0;
-            DWF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            tbest[q] = std::min(tbest[q], ms);
-        }
+    try {
+        for (int round = 0; round < 2; round++)
+            for (size_t q = 0; q < cand.size(); q++) {
+                c.tile = cand[q].tile;
+                c.gather = cand[q].gather;
+                auto run = [&]() {
+                    if (which == 0) apply_global(p, DWF_OP_DDAGD, y, x, nullptr);
+                    else apply_local(p, Ls_op, y, x, nullptr);
+                };
+                run();
+                DWF_CUDA(cudaEventRecord(ev.e0, st));
+                for (int r = 0; r < reps; r++) run();
+                DWF_CUDA(cudaEventRecord(ev.e1, st));
+                DWF_CUDA(cudaEventSynchronize(ev.e1));
+                float ms = 0;
+                DWF_CUDA(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+                tbest[q] = std::min(tbest[q], ms);
+            }
+    } catch (...) {
+        // a failed tuning run leaves the default shape, not the candidate it was timing
+        c.tile = 8;
+        c.gather = 0;
+        throw;
+    }
     KCfg bestc = c;
     float best = 1e30f;
     for (size_t q = 0; q < cand.size(); q++)
@@ -553,8 +558,6 @@ void Engine::autotune(Prec p, int which, int Ls_op, int reps)
             best = tbest[q];
             bestc = cand[q];
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c = bestc;
     c.tuned = true;
 }

@@ -11,6 +11,27 @@
 
 namespace dwf {
 
+// Two timing events, destroyed on every exit path.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventPair()
+    {
+        DWF_CUDA(cudaEventCreate(&e0));
+        const cudaError_t e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            throw CudaError{e, "cudaEventCreate"};
+        }
+    }
+    ~EventPair()
+    {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    EventPair(const EventPair &) = delete;
+    EventPair &operator=(const EventPair &) = delete;
+};
+
 // Fifth-dimension matrices of one Ls for every system, [nsys][2][Ls][Ls]
 // (chirality 0 = spins 0,1 (P_-), 1 = spins 2,3 (P_+)).
 enum MatKind {

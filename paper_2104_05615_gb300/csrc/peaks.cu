@@ -38,15 +38,6 @@ __global__ void __launch_bounds__(kThreads) fma_peak_kernel(R *sink, int iters, 
     if (s < R(-1)) sink[0] = s;
 }
 
-struct Events {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    ~Events()
-    {
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
-    }
-};
-
 template <typename R>
 double measure(dwf::Engine &E, int iters)
 {
@@ -58,9 +49,7 @@ double measure(dwf::Engine &E, int iters)
     if (per_sm < 1) per_sm = 1;
     const int blocks = sms * per_sm;  // one full wave: no tail
     R *sink = static_cast<R *>(E.ws("fma_peak_sink", 64));
-    Events ev;
-    DWF_CUDA(cudaEventCreate(&ev.e0));
-    DWF_CUDA(cudaEventCreate(&ev.e1));
+    EventPair ev;
     float best = FLT_MAX;
     for (int rep = 0; rep < 4; rep++) {  // the first is a warm-up
         DWF_CUDA(cudaEventRecord(ev.e0, E.st));

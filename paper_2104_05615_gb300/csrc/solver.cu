@@ -333,10 +333,8 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     double *bb = E.ws_d("bb", nsys), *rr = E.ws_d("rr", nsys), *rz = E.ws_d("rz", nsys);
     double *al = E.ws_d("al", nsys), *be = E.ws_d("be", nsys), *pAp = E.ws_d("pAp", nsys);
 
-    cudaEvent_t e0, e1;
-    DWF_CUDA(cudaEventCreate(&e0));
-    DWF_CUDA(cudaEventCreate(&e1));
-    DWF_CUDA(cudaEventRecord(e0, st));
+    EventPair ev;  // the solve's device time; destroyed on every exit path
+    DWF_CUDA(cudaEventRecord(ev.e0, st));
 
     for (int k = 0; k < nsys; k++) {
         const LatticeGeom &g = *E.sys[k].g;
@@ -553,13 +551,11 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
         launch_unpack(P64, xs[k], (char *)x64 + field_bytes(P64, E.sys[k].off, Ls), E.perm[k],
                       g.ne(), g.Vh, Ls, st);
     }
-    DWF_CUDA(cudaEventRecord(e1, st));
+    DWF_CUDA(cudaEventRecord(ev.e1, st));
     DWF_CUDA(cudaMemcpyAsync(h_rr.data(), rr, nsys * 8, cudaMemcpyDeviceToHost, st));
     DWF_CUDA(cudaStreamSynchronize(st));
     float ms = 0;
-    DWF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    DWF_CUDA(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
     res.iters = iters;
     res.inner_total = inner_total;
     res.ru = ru;
