@@ -34,7 +34,10 @@
  * free-field plane-wave spectrum; M5op^-1 closed form vs elimination; gauge
  * covariance; Hermitian positivity of D^+D; even-odd Schur solve vs dense LU;
  * local operator vs an independent padded-field construction and vs the
- * truncated product; CG/PCG identities; reduced-Ls identities.
+ * truncated product; the FP64 true residual vs the dense matrix; the
+ * preconditioner vs k textbook CG steps per dense block; CG/PCG identities;
+ * the (s, spin) order of T by a selection matrix; reduced-Ls identities and
+ * the reduced preconditioner as the composition of its parts.
  * Parity unpinned: outer iteration counts (the paper's ensembles are absent).
  */
 #include "dwf_oracle.h"
