@@ -32,6 +32,19 @@ struct EventPair {
     EventPair &operator=(const EventPair &) = delete;
 };
 
+class Engine;
+
+// Issues an engine's work on another stream for one scope: the engine's own
+// stream comes back on every exit path, exceptions included.
+struct StreamSwap {
+    Engine &E;
+    cudaStream_t old;
+    StreamSwap(Engine &e, void *s);
+    ~StreamSwap();
+    StreamSwap(const StreamSwap &) = delete;
+    StreamSwap &operator=(const StreamSwap &) = delete;
+};
+
 // Fifth-dimension matrices of one Ls for every system, [nsys][2][Ls][Ls]
 // (chirality 0 = spins 0,1 (P_-), 1 = spins 2,3 (P_+)).
 enum MatKind {
@@ -166,6 +179,18 @@ class Engine {
     const KCfg &kcfg(Prec p, int which, int Ls_op);
     // device flag raised by a bounded wait that gave up (reported as DWF_ETIMEOUT)
     int *err_flag = nullptr;
+    // bounded-wait policy of the stage kernels (dwf_set_wait_policy)
+    unsigned poll_limit = 0;
+    int force_timeout = 0;
+    // stage arguments common to every launch: error flag and wait policy
+    StageArgs stage_base() const
+    {
+        StageArgs a{};
+        a.err = err_flag;
+        a.poll_limit = poll_limit;
+        a.force_timeout = force_timeout;
+        return a;
+    }
     bool check_err();  // reads and clears the flag (synchronizes the stream)
 
     // reduced Ls
@@ -182,6 +207,12 @@ class Engine {
     size_t pinned_n_ = 0;
     template <class T> T *upload(const std::vector<T> &h);
 };
+
+inline StreamSwap::StreamSwap(Engine &e, void *s) : E(e), old(e.st)
+{
+    if (s) E.st = (cudaStream_t)s;
+}
+inline StreamSwap::~StreamSwap() { E.st = old; }
 
 // Solver driver (solver.cu).  xs/bs: canonical FP64 device fields per system.
 struct SolveResult {

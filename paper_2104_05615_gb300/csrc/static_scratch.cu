@@ -15,8 +15,10 @@
 
 namespace {
 
-// 24 MiB: room for the three intermediate fields of lattices up to, e.g.,
-// 8^4 x Ls = 12 in FP32 (3 x 4.7 MB) or 16^4 x Ls = 8 in FP16.
+// 24 MiB: room for the three intermediate fields (each dwf_packed_bytes, one
+// checkerboard) of lattices up to, e.g., 8^4 x Ls = 12 in FP32 (3 x 2.4 MB)
+// or 12^4 x Ls = 12 in FP16 (3 x 6.5 MB); 12^4 x Ls = 12 in FP32 (3 x 11.9 MB)
+// does not fit.
 constexpr size_t kStaticScratchBytes = 24u << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -26,7 +28,10 @@ void *g_scratch_addr[kMaxDevices] = {};  // device address of g_static_scratch p
 
 // The device address of the array on the current device.  In host code the
 // symbol is only a host-side stand-in, so its address must be looked up once
-// per device, with that device current.
+// per device, with that device current.  The address is kept for the life of
+// the process: after cudaDeviceReset (or a release of the device's primary
+// context) the module is loaded again and the kept address is stale, so this
+// entry point must not be used across a device reset.
 cudaError_t scratch_address(void **out)
 {
     int dev = 0;
@@ -81,10 +86,8 @@ extern "C" dwf_status dwf_apply_packed_static(dwf_handle *h, void *out, const vo
     }
     void *scr[3] = {base, (char *)base + fb, (char *)base + 2 * fb};
     try {
-        cudaStream_t old = E.st;
-        if (stream) E.st = (cudaStream_t)stream;
+        StreamSwap sw(E, stream);  // the handle's stream is restored on every exit path
         E.apply_global((Prec)prec, op, out, in, nullptr, scr);
-        E.st = old;
     } catch (const CudaError &e) {
         dwf_handle_set_error(h, cudaGetErrorString(e.err));
         return e.err == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
