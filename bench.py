@@ -101,12 +101,47 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "fx16": 2}
+
+
+def stage_bytes(Ls, prec):
+    """Algorithmic bytes of one fused hop stage per output 5D site (the
+    compulsory traffic: input spinor read once, output written once, the two
+    stored rows of each of the 8 links read once per Ls-slab): 24 w + 24 w +
+    8 * 12 * w / Ls, plus one FP32 scale per 4D site on each side for the
+    scaled 16-bit formats (2 * 4 / Ls).  113 B for FP16 at Ls = 12, 224 B for
+    FP32."""
+    w = STORE_BYTES[prec]
+    b = 24 * w + 24 * w + 8 * 12 * w / Ls
+    if prec in ("f16", "fx16"):
+        b += 2 * 4 / Ls
+    return b
+
+
+def local_stage_sites(geo, Ls):
+    """Output 5D sites of the four stages of one local-operator application:
+    O1 (stage 1), E2 (stage 2), O1 (stage 3) and the block interior (stage 4)."""
+    nb = geo["blocks"]
+    return nb * (2 * geo["o1_sites"] + geo["e2_sites"] + geo["block_sites"]) * Ls
+
+
 def local_op_bytes(geo, Ls, prec="f16"):
-    """Compulsory bytes of one local-operator application (four hop stages):
-    every input field read once, every output written once, aux fields read
-    once, two rows of each of the 8 links per output 4D site read once."""
-    w = {"f16": 2 * 24 + 4, "fx16": 2 * 24 + 4, "bf16": 48, "f32": 96, "f64": 192}[prec]   # bytes / 5D site
-    wl = {"f16": 2, "fx16": 2, "bf16": 2, "f32": 4, "f64": 8}[prec] * 12 * 8      # link bytes / 4D site
+    """Algorithmic bytes of one local-operator application, four stages."""
+    return stage_bytes(Ls, prec) * local_stage_sites(geo, Ls)
+
+
+def global_op_bytes(geo, Ls, prec="f32"):
+    """Algorithmic bytes of one global D^+D, four stages over the even (odd)
+    sites: 896 B per even 5D site in FP32 at Ls = 12."""
+    return stage_bytes(Ls, prec) * 4 * geo["even_sites"] * Ls
+
+
+def local_op_bytes_wide(geo, Ls, prec="f16"):
+    """The wider count of what the stages read: the per-(site, s) FP16 scales
+    of this build's format, the aux fields of stages 2 and 4 and the dot vector
+    of stage 4 (all real reads, beyond the algorithmic bytes)."""
+    w = {"f16": 2 * 24 + 4, "fx16": 2 * 24 + 4, "bf16": 48, "f32": 96, "f64": 192}[prec]
+    wl = STORE_BYTES[prec] * 12 * 8
     nb = geo["blocks"]
     I, O1, E2 = nb * geo["block_sites"], nb * geo["o1_sites"], nb * geo["e2_sites"]
     s1 = (I + O1) * Ls * w + O1 * wl
@@ -116,9 +151,9 @@ def local_op_bytes(geo, Ls, prec="f16"):
     return s1 + s2 + s3 + s4
 
 
-def global_op_bytes(geo, Ls, prec="f32"):
+def global_op_bytes_wide(geo, Ls, prec="f32"):
     w = {"f16": 52, "fx16": 52, "bf16": 48, "f32": 96, "f64": 192}[prec]
-    wl = {"f16": 2, "fx16": 2, "bf16": 2, "f32": 4, "f64": 8}[prec] * 12 * 8
+    wl = STORE_BYTES[prec] * 12 * 8
     n = geo["even_sites"]
     # S1: x -> t1 ; S2: t1, x -> w ; S3: w -> t3 ; S4: t3, w, x -> out
     return (2 + 3 + 2 + 4) * n * Ls * w + 4 * n * wl
@@ -380,6 +415,47 @@ def workload_config(name, cfg):
             "mass": cfg["mass"], "tol": cfg["tol"], "inner_iters": cfg.get("inner_iters"),
             "inner_prec": cfg.get("inner_prec"), "Ls_hat": cfg.get("Ls_hat"),
             "l2": "256 MiB buffer written between timed steps; solve working set > L2"}
+
+
+def op_roofline(geo, cfg, cfg_name, mspcg, opt):
+    """Roofline of the dominant kernel family from the in-solve operator timings:
+    the local-operator stages (inner precision, at the preconditioner's fifth
+    extent) for MSPCG, the global FP32 D^+D for plain CG; achieved = the
+    algorithmic bytes of one application / its mean in-solve duration."""
+    hbm, peak_kind = peaks()
+    inner_prec = cfg.get("inner_prec", "f32") if mspcg else "f32"
+    Ls_in = cfg.get("Ls_hat") or cfg["Ls"]
+    gbyt = global_op_bytes(geo, cfg["Ls"], "f32")
+    t_glob = opt["outer_op_ms"] / max(1, opt["outer_op_count"]) / 1e3
+    if mspcg and opt["local_op_count"]:
+        t_loc = opt["local_op_ms"] / opt["local_op_count"] / 1e3
+        byt = local_op_bytes(geo, Ls_in, inner_prec)
+        wide = local_op_bytes_wide(geo, Ls_in, inner_prec)
+        sites = local_stage_sites(geo, Ls_in)
+        kernel = (f"stage_kernel<{inner_prec}> x4: one application of the block-local D^+D "
+                  f"(snake halo) at Ls={Ls_in}, {opt['local_op_count']} applications timed in the solves")
+        traffic = recorded_traffic(f"local_{inner_prec}_{cfg_name}_bytes_per_application")
+        per_site = stage_bytes(Ls_in, inner_prec)
+    else:
+        t_loc, byt, wide = t_glob, gbyt, global_op_bytes_wide(geo, cfg["Ls"], "f32")
+        sites = 4 * geo["even_sites"] * cfg["Ls"]
+        kernel = (f"stage_kernel<f32> x4: one application of the global D^+D, "
+                  f"{opt['outer_op_count']} applications timed in the solves")
+        traffic = recorded_traffic(f"global_f32_{cfg_name}_bytes_per_application")
+        per_site = stage_bytes(cfg["Ls"], "f32")
+    achieved = byt / t_loc / 1e9 if t_loc > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None, "traffic": traffic, "kernel": kernel,
+                "algorithmic_bytes": byt, "stage_output_5d_sites": sites,
+                "bytes_per_stage_output_5d_site": per_site, "application_ms": t_loc * 1e3,
+                "bytes_with_scales_aux_dot": wide,
+                "frac_with_scales_aux_dot": (wide / t_loc / 1e9 / hbm) if t_loc > 0 else None,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
+    dslash = {"op": "global D^+D FP32 (4 fused stages), timed in the solves", "ms": t_glob * 1e3,
+              "GB_per_s": gbyt / t_glob / 1e9 if t_glob > 0 else None,
+              "frac_of_hbm": gbyt / t_glob / 1e9 / hbm if t_glob > 0 else None,
+              "algorithmic_bytes": gbyt, "applications": opt["outer_op_count"]}
+    return roofline, dslash
 
 
 def main():
@@ -672,30 +748,7 @@ def main():
     # --- dominant kernel roofline: the operator applications timed live, with
     # CUDA events on the solve's stream, over the timed solves
     geo = B.dwf_get_geometry(lat.h)
-    hbm, peak_kind = peaks()
-    opt = st["op_timing"]
-    inner_prec = cfg.get("inner_prec", "f32") if mspcg else "f32"
-    gbyt = global_op_bytes(geo, cfg["Ls"], "f32")
-    t_glob = opt["outer_op_ms"] / max(1, opt["outer_op_count"]) / 1e3
-    if mspcg and not cfg.get("Ls_hat") and opt["local_op_count"]:
-        t_loc = opt["local_op_ms"] / opt["local_op_count"] / 1e3
-        byt = local_op_bytes(geo, cfg["Ls"], inner_prec)
-        kernel = (f"stage_kernel<{inner_prec}> x4: one application of the block-local D^+D "
-                  f"(snake halo), {opt['local_op_count']} applications timed in the solves")
-        traffic = recorded_traffic(f"local_{inner_prec}_{cfg_name}_bytes_per_application")
-    else:
-        t_loc, byt = t_glob, gbyt
-        kernel = (f"stage_kernel<f32> x4: one application of the global D^+D, "
-                  f"{opt['outer_op_count']} applications timed in the solves")
-        traffic = recorded_traffic(f"global_f32_{cfg_name}_bytes_per_application")
-    achieved = byt / t_loc / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "kernel": kernel,
-                "algorithmic_bytes": byt, "application_ms": t_loc * 1e3,
-                "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
-    dslash = {"op": "global D^+D FP32 (4 fused stages), timed in the solves", "ms": t_glob * 1e3,
-              "GB_per_s": gbyt / t_glob / 1e9, "frac_of_hbm": gbyt / t_glob / 1e9 / hbm,
-              "applications": opt["outer_op_count"]}
+    roofline, dslash = op_roofline(geo, cfg, cfg_name, mspcg, st["op_timing"])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

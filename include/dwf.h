@@ -86,7 +86,10 @@ typedef struct {
     double delta;          /* reliable update when ||r|| < delta * max ||r|| since the last one */
     int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */
     int use_graph;         /* 1: capture each outer iteration in a CUDA graph */
-    int check_every;       /* host convergence check period in outer iterations (>= 1) */
+    int check_every;       /* the host reads the residual norm every check_every outer
+                              iterations (<= 1: every one) and only then decides reliable
+                              updates and convergence; the iterations in between run without
+                              a host synchronisation (up to check_every - 1 extra iterations) */
     int time_kernels;      /* 1: time every operator application with CUDA events on the
                               solve's stream (reported in dwf_stats) */
     int precond_wave;      /* blocks whose k inner iterations run together (a "wave"):
@@ -261,9 +264,11 @@ dwf_status dwf_batch_mspcg(dwf_batch *bt, double *const *xs, const double *const
  * fifth-dimension matrices and the launch configuration; this call never
  * does).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array, so calls whose
- * work overlaps on the GPU (other streams, other handles, other threads)
- * race; serialize them.  stream: 0 = the handle's stream. */
+ * before any stream capture.  The address is kept for the life of the
+ * process, so the entry point must not be used across a cudaDeviceReset (or a
+ * release of the device's primary context).  Every call shares the one array,
+ * so calls whose work overlaps on the GPU (other streams, other handles, other
+ * threads) race; serialize them.  stream: 0 = the handle's stream. */
 dwf_status dwf_apply_packed_static(dwf_handle *h, void *out_dev, const void *in_dev, dwf_op op,
                                    dwf_prec prec, void *stream);
 
@@ -289,6 +294,18 @@ dwf_status dwf_get_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind, dwf_
  * padding of every block and system) with DWF_EINVAL. */
 dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
                                  const dwf_kernel_config *c);
+
+/* Bounded device waits.  The stage kernels that stage their neighbours with
+ * bulk asynchronous copies (gather = 1 in dwf_kernel_config) wait for the
+ * copies on an mbarrier; every such wait polls at most max_polls times
+ * (max_polls <= 0: the default, 2^22) and then raises the handle's error flag,
+ * which the next synchronising call (dwf_apply, the solvers) reports as
+ * DWF_ETIMEOUT.  No wait ever traps or hangs.  force_timeout != 0 exists to
+ * test that failure path: every such kernel then waits, after all of its
+ * copies have landed, on a barrier phase that is never armed, so the wait runs
+ * out with nothing in flight; 0 restores normal operation.  The handle stays
+ * usable after a DWF_ETIMEOUT (the flag is cleared when it is reported). */
+dwf_status dwf_set_wait_policy(dwf_handle *h, long long max_polls, int force_timeout);
 
 /* Kernel launches issued by this library since load (process-wide). */
 long long dwf_kernel_launch_count(void);

@@ -99,6 +99,7 @@ def lib() -> C.CDLL:
             "dwf_set_kernel_config": (i, [vp, i, i, C.POINTER(dwf_kernel_config)]),
             "dwf_fma_peak": (i, [vp, i, C.POINTER(C.c_double)]),
             "dwf_query_geometry": (i, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(dwf_geometry)]),
+            "dwf_set_wait_policy": (i, [vp, C.c_longlong, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -315,6 +316,12 @@ def dwf_get_kernel_config(h, prec, op_kind):
 def dwf_set_kernel_config(h, prec, op_kind, tile_sites, gather):
     c = dwf_kernel_config(int(tile_sites), int(gather))
     return check(lib().dwf_set_kernel_config(h, int(prec), int(op_kind), C.byref(c)), h)
+
+
+def dwf_set_wait_policy(h, max_polls=0, force_timeout=False):
+    """Poll limit of the bounded device waits (0: default) and the test-only
+    forced time-out of the bulk-copy stage kernels."""
+    return check(lib().dwf_set_wait_policy(h, int(max_polls), int(bool(force_timeout))), h)
 
 
 def dwf_kernel_launch_count():

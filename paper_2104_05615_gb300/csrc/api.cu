@@ -49,16 +49,6 @@ dwf_status guarded(std::string *err, F &&f)
     }
 }
 
-struct StreamSwap {
-    Engine &E;
-    cudaStream_t old;
-    StreamSwap(Engine &e, void *s) : E(e), old(e.st)
-    {
-        if (s) E.st = (cudaStream_t)s;
-    }
-    ~StreamSwap() { E.st = old; }
-};
-
 }  // namespace
 
 extern "C" {
@@ -518,6 +508,15 @@ dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
     k.tile = c->tile_sites;
     k.gather = (prec == DWF_F64) ? 0 : c->gather;
     k.tuned = true;
+    return DWF_OK;
+}
+
+dwf_status dwf_set_wait_policy(dwf_handle *h, long long max_polls, int force_timeout)
+{
+    if (!h) return DWF_EINVAL;
+    if (max_polls > 0xFFFFFFFFll) return DWF_EINVAL;
+    h->E->poll_limit = max_polls > 0 ? (unsigned)max_polls : 0u;
+    h->E->force_timeout = force_timeout != 0;
     return DWF_OK;
 }
 

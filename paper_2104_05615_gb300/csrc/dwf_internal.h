@@ -70,6 +70,9 @@ struct StageArgs {
     int aux_stride;      // aux sites per segment
     int aux_valid;       // aux present for local index < aux_valid
     int *err;            // device flag set when a bounded wait gives up (may be null)
+    unsigned poll_limit; // polls of a bounded wait before it gives up (0: 2^22)
+    int force_timeout;   // testing the failure path: after its copies have landed the
+                         // CTA waits on a barrier phase that never completes
     int gather;          // 0: direct neighbour loads; 1: bulk-copy staging in shared memory
     const int *active;   // per system: 0 = converged, its CTAs exit at once (null: all active)
     long site0;          // first output site of this launch (a wave of blocks); indices stay absolute

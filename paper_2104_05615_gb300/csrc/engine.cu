@@ -478,8 +478,7 @@ static void set_mats(StageArgs &a, const Mats &m, Prec p, MatKind f, MatKind g, 
 void Engine::apply_5d(Prec p, int L, MatKind k, void *out, const void *in, long nsite)
 {
     const Mats &m = mats(L);
-    StageArgs a{};
-    a.err = err_flag;
+    StageArgs a = stage_base();
     a.in = in;
     a.out = out;
     a.mphi = m.mphi;
@@ -580,8 +579,7 @@ int Engine::apply_global(Prec p, dwf_op op, void *out, const void *in, double *d
     const KCfg kc = kcfg(p, 0, Ls);
     const int tile = kc.tile;
 
-    StageArgs base{};
-    base.err = err_flag;
+    StageArgs base = stage_base();
     base.gather = kc.gather;
     base.active = active;
     base.tile_sys = tsys_e;
@@ -673,8 +671,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     const int tile = kc.tile;
     const long nI = (long)nblk * Nb_pad;
 
-    StageArgs a{};
-    a.err = err_flag;
+    StageArgs a = stage_base();
     a.gather = kc.gather;
     a.active = active;
     a.mphi = m.mphi;
@@ -695,8 +692,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     set_mats(a, m, p, MK_S1F, MK_N, TC_S1);
     launch_stage(p, MODE_F, in_mphi == nullptr, a, st);
     // S2: E2 <- O1, aux = interior x
-    StageArgs b2{};
-    b2.err = err_flag;
+    StageArgs b2 = stage_base();
     b2.gather = kc.gather;
     b2.active = active;
     b2.mphi = m.mphi;
@@ -720,8 +716,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     set_mats(b2, m, p, MK_S2GF, MK_M5ID, TC_S2G);
     launch_stage(p, MODE_S2, false, b2, st);
     // S3: O1 <- E2 (dagger)
-    StageArgs b3{};
-    b3.err = err_flag;
+    StageArgs b3 = stage_base();
     b3.gather = kc.gather;
     b3.active = active;
     b3.mphi = m.mphi;
@@ -742,8 +737,7 @@ int Engine::apply_local(Prec p, int L, void *out, const void *in, double *dot_pa
     b3.dagger = 1;
     launch_stage(p, MODE_F, false, b3, st);
     // S4: interior <- O1 (dagger), aux = w
-    StageArgs b4{};
-    b4.err = err_flag;
+    StageArgs b4 = stage_base();
     b4.gather = kc.gather;
     b4.active = active;
     b4.Ls = L;

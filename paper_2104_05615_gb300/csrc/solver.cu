@@ -480,11 +480,21 @@ dwf_status solve_impl(Engine &E, double *const *xs, const double *const *bs,
     CapturedGraph g1, g2;
     double t_local = 0, t_outer = 0;
     long long n_local = 0, n_outer = 0;
+    // the host reads |r|^2 (and decides reliable updates and convergence) only
+    // every check_every iterations; in between the iterations are issued
+    // back to back without a host synchronisation
+    const int check_every = P.check_every > 1 ? P.check_every : 1;
     while (!converged && iters < maxiter) {
         const bool graph = P.use_graph && iters > 0;
         g1.run(st, graph, half1);
         E.timed_mark(0, 1);
         iters++;
+        if (iters % check_every != 0 && iters < maxiter) {
+            g2.run(st, graph, half2);
+            if (use_precond) E.timed_mark(1, P.inner_iters);
+            if (use_precond) inner_total += P.inner_iters;
+            continue;
+        }
         DWF_CUDA(cudaStreamSynchronize(st));
         // the previous preconditioner call and this outer operator have completed
         E.timed_collect(t_outer, n_outer, t_local, n_local);

@@ -85,14 +85,19 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly),
-// records the failure and lets the CTA finish (results are then invalid and
-// the host reports DWF_ETIMEOUT).
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err)
+// Bounded wait: gives up after `limit` polls (0: 2^22; each poll may suspend
+// briefly), records the failure and lets the CTA finish (results are then
+// invalid and the host reports DWF_ETIMEOUT).  Returns whether the phase
+// completed.
+constexpr uint32_t kDefaultPollLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err,
+                                                  uint32_t limit = 0)
 {
-    for (uint32_t it = 0; it < (1u << 22); it++)
-        if (mbar_try_wait(bar, phase)) return;
+    const uint32_t n = limit ? limit : kDefaultPollLimit;
+    for (uint32_t it = 0; it < n; it++)
+        if (mbar_try_wait(bar, phase)) return true;
     if (err) atomicExch(err, 1);
+    return false;
 }
 
 // ------------------------------------------------------------- helpers
@@ -532,7 +537,10 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             }
         }
         if (!kTC) stage_mats();
-        mbar_wait_bounded(bar, 0, a.err);
+        mbar_wait_bounded(bar, 0, a.err, a.poll_limit);
+        // testing the failure path: every copy has landed (phase 0 is
+        // complete); phase 1 is never armed, so this wait runs out
+        if (a.force_timeout) mbar_wait_bounded(bar, 1, a.err, a.poll_limit);
         // rebuild the third row of each staged link
         for (int e = tid; e < TS * 8; e += nthr) {
             const int j = e >> 3, k = e & 7;

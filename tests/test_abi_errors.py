@@ -49,6 +49,7 @@ def test_null_handle_is_rejected(lib):
         "dwf_get_kernel_config": (None, B.DWF_F32, 0, C.byref(kc)),
         "dwf_set_kernel_config": (None, B.DWF_F32, 0, C.byref(kc)),
         "dwf_batch_mspcg": (None, None, None, C.byref(p), None, C.byref(st)),
+        "dwf_set_wait_policy": (None, 0, 0),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == E, name

@@ -38,3 +38,20 @@ def test_clock_summary_flags_throttling(tmp_path):
     s = c.summary()
     assert s["sm_max_mhz"] == 2070 and s["sm_mhz"] == 1800
     assert set(s["reasons"]) == {"sw_power_cap", "hw_thermal_slowdown"}
+
+
+def test_algorithmic_bytes_follow_the_stage_count():
+    """Per output 5D site a hop stage moves 24 w in + 24 w out + 8 * 12 * w / Ls
+    of links (+ 8 / Ls of FP32 scales for the scaled 16-bit formats): 113 B in
+    FP16 and 224 B in FP32 at Ls = 12.  One global D^+D is four stages over
+    the even sites (896 B per even 5D site in FP32); one local operator is the
+    four stages over O1, E2, O1 and the block interior."""
+    b = _bench()
+    assert abs(b.stage_bytes(12, "f16") - 113.0) < 0.5
+    assert b.stage_bytes(12, "bf16") == 112.0
+    assert b.stage_bytes(12, "f32") == 224.0
+    assert b.stage_bytes(8, "bf16") == 120.0
+    geo = {"blocks": 32, "block_sites": 2048, "o1_sites": 4096, "e2_sites": 6912, "even_sites": 65536}
+    assert b.global_op_bytes(geo, 12, "f32") == 896 * 65536 * 12
+    assert b.local_stage_sites(geo, 12) == 32 * (4096 + 6912 + 4096 + 2048) * 12
+    assert abs(b.local_op_bytes(geo, 12, "f16") / 6586368 - b.stage_bytes(12, "f16")) < 1e-9

@@ -89,3 +89,51 @@ def test_batched_workload_full_size_sampled(orc):
             assert o.true_residual(xs[k].cpu().numpy(), bs[k].cpu().numpy()) <= 1e-9 * 1.01, k
     finally:
         B.dwf_batch_destroy(bt)
+
+
+def _solve_full_size(name):
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import Lattice, PREC, heuristic_T
+    cfg = inputs.CONFIGS[name]
+    U = inputs.gauge_field(cfg["dims"], cfg["eps"], cfg["gauge_seed"])
+    lat = Lattice(cfg["dims"], cfg["Ls"], cfg["b"], cfg["c"], cfg["M5"], cfg["mass"], U, cfg["sub"])
+    if cfg.get("Ls_hat"):
+        lat.set_reduced_ls(cfg["Ls_hat"], heuristic_T(cfg["Ls"], cfg["Ls_hat"]), cfg["mu"])
+    b = inputs.gaussian_spinor_cb(cfg["dims"], cfg["Ls"], cfg["src_seed"])
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    # the bench's solver parameters for the workload
+    p = B.default_params(tol=cfg["tol"], maxiter=100000, inner_iters=cfg["inner_iters"],
+                         inner_prec=PREC[cfg["inner_prec"]], outer_prec=PREC[cfg["outer_prec"]],
+                         use_reduced_ls=1 if cfg.get("Ls_hat") else 0)
+    st = B.dwf_mspcg(lat.h, x, bd, p)
+    xh = x.cpu().numpy()
+    lat.close()
+    del x, bd
+    torch.cuda.empty_cache()
+    return cfg, U, b, xh, st
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_c3_full_size_mspcg_solution_oracle_residual(orc):
+    """The 16^3 x 32, Ls = 12 MSPCG solve (32 blocks of 8^4, k = 6, FP16 inner,
+    FP32 outer with FP64 reliable updates), judged by the FP64 oracle's own
+    true residual |b - D^+D x| / |b| on the host."""
+    cfg, U, b, x, st = _solve_full_size("C3")
+    assert st.converged and st.true_residual <= cfg["tol"]
+    o = orc.from_config(cfg, U)
+    assert o.true_residual(x, b) <= cfg["tol"] * 1.01
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_c4_full_size_reduced_ls_mspcg_solution_oracle_residual(orc):
+    """The 32^3 x 64, Ls = 16 MSPCG solve with the reduced-Ls preconditioner
+    (L^s = 8, BF16 inner, 32 blocks of 16^4), judged by the FP64 oracle's true
+    residual on the host (one oracle D^+D of the full lattice: a few GB of host
+    memory and tens of seconds on the host cores)."""
+    cfg, U, b, x, st = _solve_full_size("C4")
+    assert st.converged and st.true_residual <= cfg["tol"]
+    o = orc.from_config(cfg, U)
+    assert o.true_residual(x, b) <= cfg["tol"] * 1.01
