@@ -280,7 +280,10 @@ const char *dwf_batch_last_error(const dwf_batch *bt);
  * precision.  tile_sites: output 4D sites per CTA (each CTA holds their whole
  * Ls-slab); gather: 0 = neighbour spinors loaded by each thread, 1 = bulk
  * asynchronous copies (TMA engine) of whole neighbour Ls-columns into shared
- * memory.  By default the first use of an operator in a precision times every
+ * memory, 2 = the hop itself on the tensor cores (16-bit storage only, 8-site
+ * tiles, Ls in {4, 8, 12, 16}: per site the projected neighbour spinors,
+ * rows (spin, slice) x columns (direction, colour), times the links, FP16
+ * operands and FP32 accumulation).  By default the first use of an operator in a precision times every
  * candidate that fits and keeps the fastest (the autotuner, Sec. 3.1.3 tunes
  * block sizes the same way). */
 typedef struct {

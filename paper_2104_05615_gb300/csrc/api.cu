@@ -498,7 +498,7 @@ dwf_status dwf_set_kernel_config(dwf_handle *h, dwf_prec prec, int op_kind,
                                  const dwf_kernel_config *c)
 {
     if (!h || !c || !prec_ok(prec) || op_kind < 0 || op_kind > 1) return DWF_EINVAL;
-    if (c->tile_sites < 2 || c->tile_sites % 2 || (c->gather != 0 && c->gather != 1)) return DWF_EINVAL;
+    if (c->tile_sites < 2 || c->tile_sites % 2 || c->gather < 0 || c->gather > 2) return DWF_EINVAL;
     const long seg = op_kind == 0 ? h->E->ne : (long)h->E->Nb_pad;
     if (seg % c->tile_sites || !stage_fits((Prec)prec, c->tile_sites, h->Ls, c->gather)) {
         h->err = "kernel configuration does not fit";

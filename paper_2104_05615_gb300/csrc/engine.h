@@ -55,6 +55,7 @@ enum MatKind {
     MK_S4F,      // M_phi^+
     MK_S4G,      // M5op^+
     MK_S2GF,     // M5^-+ M5^-1
+    MK_MPHI,     // M_phi
     MK_N
 };
 // Operand A of the tensor-core products: [G | -F] (or F alone) in FP16,
@@ -68,6 +69,7 @@ enum TcKind {
     TC_S4,       // [M5op^+ | -M_phi^+]
     TC_M5I,      // M5^-1
     TC_M5ID,     // M5^-+
+    TC_MPHI,     // M_phi
     TC_N
 };
 struct Mats {

@@ -441,12 +441,13 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
     const int jl = tid / Ls;
     const int s = tid - jl * Ls;
     const bool active = jl < TS;
-    const long i0 = (long)blockIdx.x * TS;
+    const long i0 = a.site0 + (long)blockIdx.x * TS;  // absolute: launches may cover a site range
     const long i = i0 + (active ? jl : 0);
+    const long cta = i0 / TS;                         // absolute CTA index (dot partials)
     const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
     if (a.active && !a.active[sys]) {
         // a converged system of a batch: nothing to do (whole CTA, one system)
-        if (kMode == MODE_S4 && a.dot_part && tid == 0) a.dot_part[blockIdx.x] = 0.0;
+        if (kMode == MODE_S4 && a.dot_part && tid == 0) a.dot_part[cta] = 0.0;
         return;
     }
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
@@ -1034,7 +1035,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             double v = tid < (nthr + 31) / 32 ? red[tid] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (tid == 0) a.dot_part[blockIdx.x] = v;
+            if (tid == 0) a.dot_part[cta] = v;
         }
     }
 }
@@ -1060,7 +1061,9 @@ static void launch_t(const StageArgs &a, cudaStream_t st)
         attr_set = true;
     }
     if (L.total > 220 * 1024) throw std::runtime_error("stage tile does not fit in shared memory");
-    const long nblk = a.nout / TS;
+    const long end = a.site_end ? a.site_end : a.nout;
+    const long nblk = (end - a.site0) / TS;
+    if (nblk <= 0) return;
     stage_kernel<T, kMode, kMphi, kStage, kDag, LS, TSC><<<(unsigned)nblk, nthr, L.total, st>>>(a);
     DWF_CUDA(cudaGetLastError());
     count_launch();

@@ -211,7 +211,7 @@ def test_every_kernel_config_matches_oracle(orc, prec):
     xin = to_numpy(xd)
     want = {"DdagD": o.DdagD(xin), "local": o.local_DdagD(xin, sub)}
     ran = set()
-    for gather in (0, 1):
+    for gather in (0, 1, 2):
         for tile in (4, 8, 16, 32):
             for kind, op in ((0, "DdagD"), (1, "local")):
                 try:
@@ -225,3 +225,27 @@ def test_every_kernel_config_matches_oracle(orc, prec):
     assert {("DdagD", 0), ("local", 0)} <= ran
     if prec != "f64":
         assert {("DdagD", 1), ("local", 1)} <= ran
+    if prec in ("f16", "bf16", "fx16"):
+        assert {("DdagD", 2), ("local", 2)} <= ran
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", [n for n, c in CASES.items() if c[1] % 4 == 0])
+@pytest.mark.parametrize("prec", ["f16", "bf16", "fx16"])
+def test_tensor_core_hop_parity(orc, name, prec):
+    """The hop on the tensor cores (gather 2: projected neighbour spinors x
+    links as FP16 mma with FP32 accumulation) for D, D^+, D^+D and the local
+    operator against the oracle, on every lattice whose Ls it takes."""
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import PREC, to_device, to_numpy
+    lat, o, x, sub = setup_case(orc, name)
+    for kind in (0, 1):
+        B.dwf_set_kernel_config(lat.h, PREC[prec], kind, 8, 2)
+    xd = to_device(x, prec)
+    xin = to_numpy(xd)
+    ref = {"D": o.D(xin), "Ddag": o.D(xin, dagger=True), "DdagD": o.DdagD(xin),
+           "local": o.local_DdagD(xin, sub)}
+    for op, want in ref.items():
+        e = relerr(to_numpy(lat.apply(op, xd, prec)), want)
+        assert e < TOL[prec], f"{name} {prec} {op}: relative error {e:.3e}"
+    assert B.dwf_get_kernel_config(lat.h, PREC[prec], 1)["gather"] == 2
