@@ -136,6 +136,8 @@ __device__ __forceinline__ void load_U<double>(const double *sU, double *u)
 // (re, re), (-im, im).  chi = U h in half2, then accumulated in FP32 with the
 // neighbour's weight w (scale times boundary sign).
 __device__ __forceinline__ __half2 swap_h2(__half2 z) { return __lowhigh2highlow(z); }
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ __half2 u2h(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
 
 template <int MU, int SG>
 __device__ __forceinline__ void hop_dir_h2(const __half2 *p, const __half2 *U2, float w, float *acc)
@@ -182,6 +184,95 @@ __device__ __forceinline__ void hop_dir_h2(const __half2 *p, const __half2 *U2, 
         }
     }
     accumulate_ct<MU, SG, float>(chi, acc);
+}
+
+// The same direction accumulated in half2: acc2[spin*3 + colour] += w2 (chi
+// rebuilt to four spins), with w2 the neighbour's weight relative to the
+// site's reference scale (|w| <= 1), so the eight directions sum to at most a
+// few tens in FP16; the caller converts to FP32 and multiplies by the
+// reference once.
+template <int MU, int SG>
+__device__ __forceinline__ void hop_dir_h2_acc(const __half2 *p, const __half2 *U2, __half2 w2, __half2 *acc2)
+{
+    const __half2 ipos = __floats2half2_rn(-1.f, 1.f);
+    const __half2 ineg = __floats2half2_rn(1.f, -1.f);
+    __half2 h[6];  // h[sp*3 + c]
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const __half2 p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+        if constexpr (MU == 0) {  // h0 = p0 + SG i p3, h1 = p1 + SG i p2
+            h[c] = __hfma2(swap_h2(p3), SG > 0 ? ipos : ineg, p0);
+            h[3 + c] = __hfma2(swap_h2(p2), SG > 0 ? ipos : ineg, p1);
+        } else if constexpr (MU == 1) {  // h0 = p0 + SG p3, h1 = p1 - SG p2
+            h[c] = SG > 0 ? __hadd2(p0, p3) : __hsub2(p0, p3);
+            h[3 + c] = SG > 0 ? __hsub2(p1, p2) : __hadd2(p1, p2);
+        } else if constexpr (MU == 2) {  // h0 = p0 + SG i p2, h1 = p1 - SG i p3
+            h[c] = __hfma2(swap_h2(p2), SG > 0 ? ipos : ineg, p0);
+            h[3 + c] = __hfma2(swap_h2(p3), SG > 0 ? ineg : ipos, p1);
+        } else {  // h0 = p0 + SG p2, h1 = p1 + SG p3
+            h[c] = SG > 0 ? __hadd2(p0, p2) : __hsub2(p0, p2);
+            h[3 + c] = SG > 0 ? __hadd2(p1, p3) : __hsub2(p1, p3);
+        }
+    }
+    __half2 hs[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) hs[q] = swap_h2(h[q]);
+    // the link's 18 half2 (a 16-byte aligned 80-byte slot) in five wide loads
+    __half2 U[18];
+    {
+        const uint4 *u4 = reinterpret_cast<const uint4 *>(U2);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint4 w = u4[q];
+            U[4 * q] = u2h(w.x);
+            U[4 * q + 1] = u2h(w.y);
+            U[4 * q + 2] = u2h(w.z);
+            U[4 * q + 3] = u2h(w.w);
+        }
+        const uint2 w = reinterpret_cast<const uint2 *>(U2)[8];
+        U[16] = u2h(w.x);
+        U[17] = u2h(w.y);
+    }
+    __half2 chi[6];  // [sp][row]
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        const __half2 *Ur = U + r * 6;
+#pragma unroll
+        for (int sp = 0; sp < 2; sp++) {
+            __half2 t = __hmul2(Ur[0], h[sp * 3]);
+            t = __hfma2(Ur[1], hs[sp * 3], t);
+            t = __hfma2(Ur[2], h[sp * 3 + 1], t);
+            t = __hfma2(Ur[3], hs[sp * 3 + 1], t);
+            t = __hfma2(Ur[4], h[sp * 3 + 2], t);
+            t = __hfma2(Ur[5], hs[sp * 3 + 2], t);
+            chi[sp * 3 + r] = t;
+        }
+    }
+    // spins 0, 1: + w chi; spins 2, 3 rebuilt (the reconstruction of
+    // accumulate_ct): MU=x (-SG i c1, -SG i c0), y (-SG c1, SG c0),
+    // z (-SG i c0, SG i c1), t (SG c0, SG c1); -i z = swap(z) (1, -1)
+    const __half2 wn = __hneg2(w2);
+    const __half2 wmi = __hmul2(w2, ineg);  // w times -i acting on a swapped value
+    const __half2 wpi = __hmul2(w2, ipos);  // w times +i acting on a swapped value
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const __half2 c0 = chi[c], c1 = chi[3 + c];
+        acc2[c] = __hfma2(w2, c0, acc2[c]);
+        acc2[3 + c] = __hfma2(w2, c1, acc2[3 + c]);
+        if constexpr (MU == 0) {
+            acc2[6 + c] = __hfma2(SG > 0 ? wmi : wpi, swap_h2(c1), acc2[6 + c]);
+            acc2[9 + c] = __hfma2(SG > 0 ? wmi : wpi, swap_h2(c0), acc2[9 + c]);
+        } else if constexpr (MU == 1) {
+            acc2[6 + c] = __hfma2(SG > 0 ? wn : w2, c1, acc2[6 + c]);
+            acc2[9 + c] = __hfma2(SG > 0 ? w2 : wn, c0, acc2[9 + c]);
+        } else if constexpr (MU == 2) {
+            acc2[6 + c] = __hfma2(SG > 0 ? wmi : wpi, swap_h2(c0), acc2[6 + c]);
+            acc2[9 + c] = __hfma2(SG > 0 ? wpi : wmi, swap_h2(c1), acc2[9 + c]);
+        } else {
+            acc2[6 + c] = __hfma2(SG > 0 ? w2 : wn, c0, acc2[6 + c]);
+            acc2[9 + c] = __hfma2(SG > 0 ? w2 : wn, c1, acc2[9 + c]);
+        }
+    }
 }
 
 // Decode the NC 16-byte chunks of one 5D spinor (stride `cs` chunks apart);
@@ -610,6 +701,34 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         }
         const int sp = s + 1 < Ls ? s + 1 : 0;
         const int sm1 = s > 0 ? s - 1 : Ls - 1;
+        // the site's eight neighbour entries in two 16-byte shared loads
+        int nb8[8];
+        {
+            const int4 *q = reinterpret_cast<const int4 *>(sN + jl * 8);
+            const int4 x0 = q[0], x1 = q[1];
+            nb8[0] = x0.x; nb8[1] = x0.y; nb8[2] = x0.z; nb8[3] = x0.w;
+            nb8[4] = x1.x; nb8[5] = x1.y; nb8[6] = x1.z; nb8[7] = x1.w;
+        }
+        // FP16 path: the eight directions accumulate in half2 relative to the
+        // largest neighbour scale at this (site, s)
+        float scl[8];
+        float inv_ref = 0.f, ref = 0.f;
+        __half2 acc2[12];
+        if constexpr (kH2) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int e = nb8[k];
+                scl[k] = 0.f;
+                if (e != -1) {
+                    const long idx = e >= 0 ? (long)e : (long)(-e - 2);
+                    scl[k] = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
+                    ref = fmaxf(ref, scl[k]);
+                }
+            }
+            inv_ref = ref > 0.f ? __fdividef(1.f, ref) : 0.f;
+#pragma unroll
+            for (int q = 0; q < 12; q++) acc2[q] = __float2half2_rn(0.f);
+        }
         // one direction k = 2 mu + d with compile-time mu and projector sign:
         // forward (d = 0) 1 - gamma, backward 1 + gamma, flipped for D^w^+
         auto dir = [&](auto kc) {
@@ -619,7 +738,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             // fixed point: the projection takes the offset of the biased
             // integers off itself (exactly), except where M_phi mixes slices
             constexpr bool kFxB = (T::P == PFX16) && !kMphi;
-            const int e = sN[jl * 8 + k];
+            const int e = nb8[k];
             if (e == -1) return;
             const long idx = e >= 0 ? (long)e : (long)(-e - 2);
             R psi[24];
@@ -658,10 +777,10 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 uint4 raw[NC];
 #pragma unroll
                 for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + s);
-                sc = __ldg(scale_ptr<TF16>(a.in, a.nin, Ls) + idx * Ls + s);
-                hop_dir_h2<mu, SG>(reinterpret_cast<const __half2 *>(raw),
-                                   reinterpret_cast<const __half2 *>(sU + (jl * 8 + k) * kLinkStride),
-                                   e >= 0 ? sc : -sc, acc);
+                const float w = (e >= 0 ? scl[k] : -scl[k]) * inv_ref;
+                hop_dir_h2_acc<mu, SG>(reinterpret_cast<const __half2 *>(raw),
+                                       reinterpret_cast<const __half2 *>(sU + (jl * 8 + k) * kLinkStride),
+                                       __float2half2_rn(w), acc2);
                 return;
             } else {
                 const uint4 *gp = reinterpret_cast<const uint4 *>(a.in) + (size_t)idx * NC * Ls;
@@ -706,6 +825,14 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         dir(std::integral_constant<int, 5>{});
         dir(std::integral_constant<int, 6>{});
         dir(std::integral_constant<int, 7>{});
+        if constexpr (kH2) {
+#pragma unroll
+            for (int q = 0; q < 12; q++) {
+                const float2 f = __half22float2(acc2[q]);
+                acc[2 * q] = f.x * ref;
+                acc[2 * q + 1] = f.y * ref;
+            }
+        }
     }
 
     // own aux column; the S2 tensor-core stage on FP16 storage keeps it as
@@ -858,11 +985,6 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         const int npair = TS * 12 / 16;  // pairs of 8-column n-tiles per chirality
         const int nunit = 2 * npair;
         const uint4 *Af = reinterpret_cast<const uint4 *>(a.F) + (size_t)sys * 2 * 2 * 32;
-        uint4 af[2][2];  // A fragments of this lane: [chi][k-step]
-#pragma unroll
-        for (int chi = 0; chi < 2; chi++)
-#pragma unroll
-            for (int kk = 0; kk < nk; kk++) af[chi][kk] = __ldg(Af + ((chi * 2 + kk) * 32 + lane));
         // this lane's ldmatrix row: slice lr of n-tile ln / 8 of the pair
         const int lr = (lane & 7) + 8 * ((lane >> 3) & 1);
         const int ln = 8 * (lane >> 4);
@@ -875,11 +997,13 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
 #pragma unroll
             for (int kk = 0; kk < nk; kk++) {
                 if (kAux && kk == 0 && !aux_tile) continue;  // aux all zero in this tile
+                // A fragment of this lane, [G | -F] of this chirality and k-step
+                const uint4 af = __ldg(Af + ((chi * 2 + kk) * 32 + lane));
                 const __half *tb = sB + ((size_t)(kk * 2 + chi) * 16 + lr) * RS + pr * 16 + ln;
                 uint32_t b0, b1, b2, b3;
                 ldmatrix_x4_trans(smem_u32(tb), b0, b1, b2, b3);
-                mma_16816(d, af[chi][kk], b0, b1);
-                mma_16816(d + 4, af[chi][kk], b2, b3);
+                mma_16816(d, af, b0, b1);
+                mma_16816(d + 4, af, b2, b3);
             }
         };
         auto unit_store = [&](int u, const float *d) {
@@ -889,14 +1013,25 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             for (int h = 0; h < 2; h++) {
                 const int nd = pr * 16 + h * 8 + 2 * tg;
                 const int jd = nd / 12, rd = chi * 12 + (nd - jd * 12);
-                // FP16 storage folds the site scale into the stored scale
-                const float sd = kScale ? 1.f : sMax[jd];
-                if (g < Ls)
-                    *reinterpret_cast<float2 *>(sD + (jd * Ls + g) * 24 + rd) =
-                        make_float2(d[4 * h] * sd, d[4 * h + 1] * sd);
-                if (g + 8 < Ls)
-                    *reinterpret_cast<float2 *>(sD + (jd * Ls + g + 8) * 24 + rd) =
-                        make_float2(d[4 * h + 2] * sd, d[4 * h + 3] * sd);
+                if constexpr (kScale) {
+                    // scaled formats: D is normalised by the site scale (which
+                    // goes into the stored scale), so it is kept as FP16
+                    __half *sDh = reinterpret_cast<__half *>(sD);
+                    if (g < Ls)
+                        *reinterpret_cast<uint32_t *>(sDh + (jd * Ls + g) * 24 + rd) =
+                            pack_h2(d[4 * h], d[4 * h + 1]);
+                    if (g + 8 < Ls)
+                        *reinterpret_cast<uint32_t *>(sDh + (jd * Ls + g + 8) * 24 + rd) =
+                            pack_h2(d[4 * h + 2], d[4 * h + 3]);
+                } else {
+                    const float sd = sMax[jd];
+                    if (g < Ls)
+                        *reinterpret_cast<float2 *>(sD + (jd * Ls + g) * 24 + rd) =
+                            make_float2(d[4 * h] * sd, d[4 * h + 1] * sd);
+                    if (g + 8 < Ls)
+                        *reinterpret_cast<float2 *>(sD + (jd * Ls + g + 8) * 24 + rd) =
+                            make_float2(d[4 * h + 2] * sd, d[4 * h + 3] * sd);
+                }
             }
         };
         if (alias) {
@@ -923,14 +1058,21 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         }
         __syncthreads();
         if (active) {
-            const float4 *q4 = reinterpret_cast<const float4 *>(sD + (jl * Ls + s) * 24);
+            if constexpr (kScale) {
+                const uint4 *q4 = reinterpret_cast<const uint4 *>(reinterpret_cast<const __half *>(sD) +
+                                                                  (jl * Ls + s) * 24);
 #pragma unroll
-            for (int c = 0; c < 6; c++) {
-                float4 f = q4[c];
-                out[4 * c] = f.x;
-                out[4 * c + 1] = f.y;
-                out[4 * c + 2] = f.z;
-                out[4 * c + 3] = f.w;
+                for (int c = 0; c < 3; c++) unpack8(q4[c], out + 8 * c, __half());
+            } else {
+                const float4 *q4 = reinterpret_cast<const float4 *>(sD + (jl * Ls + s) * 24);
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    float4 f = q4[c];
+                    out[4 * c] = f.x;
+                    out[4 * c + 1] = f.y;
+                    out[4 * c + 2] = f.z;
+                    out[4 * c + 3] = f.w;
+                }
             }
         }
     } else {

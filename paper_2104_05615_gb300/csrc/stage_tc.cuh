@@ -67,8 +67,6 @@ __host__ __device__ inline TcSmem tc_smem(int Ls, bool has_aux, bool fifth_tc)
     return m;
 }
 
-__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
-__device__ __forceinline__ __half2 u2h(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
 
 // Sixteen-byte ldmatrix of an m16n8k16 A fragment: lane l supplies row l % 16,
 // column block l / 16 of the 16 x 16 tile at `base` (row pitch kPhiRow halves).
