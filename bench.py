@@ -281,17 +281,20 @@ def cpu_baseline(cfg, b, gpu_iters, k, budget_s=20.0):
     o.DdagD(b)
     t_app = time.perf_counter() - t0
     nblk = int(np.prod([d // s for d, s in zip(cfg["dims"], cfg["sub"])]))
-    per_iter = t_app * (1 + (k * nblk if cfg["solver"] == "mspcg" else 0))
+    # the inner applications run at the reduced fifth extent when there is one
+    red = (cfg.get("Ls_hat") or cfg["Ls"]) / cfg["Ls"]
+    n_app = 1 + (k * nblk * red if cfg["solver"] == "mspcg" else 0)
+    per_iter = t_app * n_app
     return {"value": per_iter * gpu_iters, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"one FP64 oracle D^+D on the full {cfg['dims']} x Ls={cfg['Ls']} lattice "
-                       f"({t_app:.2f} s), x (1 + k*blocks) = {1 + k * nblk} per MSPCG outer iteration, "
+                       f"({t_app:.2f} s), x (1 + k*blocks*Ls_inner/Ls) = {n_app:g} per outer iteration, "
                        f"x {gpu_iters} outer iterations (extrapolated)")}
 
 
 # Outer MSPCG iterations to tol on each MSPCG workload (measured: 16^3x32 Ls=12
 # with FP16 inner; 32^3x64 Ls=16 with reduced Ls), used to extrapolate the
 # oracle's time to solution from its timed operator applications.
-REF_OUTER_ITERS = {"C3": 732, "C4": 1725}
+REF_OUTER_ITERS = {"C3": 732, "C4": 1597}
 
 
 def run_reference(args, cfg_name, rank):
@@ -458,6 +461,56 @@ def op_roofline(geo, cfg, cfg_name, mspcg, opt):
     return roofline, dslash
 
 
+def config_record(name, args, device, flush, barrier, maxall, rank):
+    """A second configuration in the same line: one timed MSPCG solve and one
+    timed plain-CG solve of the workload (after a short warm-up that runs the
+    autotuner, allocates the workspaces and captures the graphs), with the
+    in-solve operator roofline and the oracle on the host cores."""
+    import torch
+    from paper_2104_05615_gb300 import binding as B
+    cfg, lat, b, bd = setup(name, device)
+    rec = {"config": workload_config(name, cfg)}
+    try:
+        for mspcg in (True, False):
+            warm = solver_params(cfg, mspcg)
+            warm.maxiter = 3
+            x = torch.zeros_like(bd)
+            (B.dwf_mspcg if mspcg else B.dwf_cg)(lat.h, x, bd, warm, raise_on_noconv=False)
+            del x
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            times, st, x, launches = time_solves(lat, bd, solver_params(cfg, True), True, 1, 0, flush, barrier)
+        del x
+        ct, cst, x, _ = time_solves(lat, bd, solver_params(cfg, False), False, 1, 0, flush, barrier)
+        del x
+        t, tcg = maxall(times[0]), maxall(ct[0])
+        geo = B.dwf_get_geometry(lat.h)
+        roofline, dslash = op_roofline(geo, cfg, name, True, st["op_timing"])
+        rec.update({"value": t, "unit": "s",
+                    "solver": {"outer_iters": st["outer_iters"], "inner_iters_total": st["inner_iters_total"],
+                               "reliable_updates": st["reliable_updates"], "true_residual": st["true_residual"],
+                               "reduced_ls": {"Ls_hat": cfg.get("Ls_hat"), "mu": cfg.get("mu"),
+                                              "T": "heuristic (the L^s/2 slices next to each wall)"}},
+                    "baseline_cg": {"seconds": tcg, "outer_iters": cst["outer_iters"],
+                                    "reliable_updates": cst["reliable_updates"],
+                                    "true_residual": cst["true_residual"]},
+                    "speedup_vs_cg": tcg / t, "gpu_launches": launches, "clocks": clk.summary(),
+                    "roofline": roofline, "dslash": dslash,
+                    "ms_per_outer_iteration": {"mspcg": t * 1e3 / max(1, st["outer_iters"]),
+                                               "cg": tcg * 1e3 / max(1, cst["outer_iters"])}})
+        iters = st["outer_iters"]
+    finally:
+        lat.close()
+        del bd
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            rec["cpu_baseline"] = cpu_baseline(cfg, b, iters, cfg.get("inner_iters", 0))
+        except Exception as e:  # the oracle is test infrastructure; report, don't fail
+            rec["cpu_baseline"] = {"value": None, "unit": "s", "cores": None, "kind": "oracle",
+                                   "sample": f"failed: {e}"}
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,6 +520,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-c4", action="store_true",
+                    help="skip the record of the 32^3 x 64, Ls = 16 workload (one timed solve each)")
     ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves", "inner", "train"],
                     help="ops: only apply the operators (for profilers); inner: outer iterations "
                          "and time to solution against the inner iteration count and precision")
@@ -757,6 +812,12 @@ def main():
         except Exception as e:  # the oracle is test infrastructure; report, don't fail
             cpu = {"value": None, "unit": "s", "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
+    # --- the largest single-GPU configuration (32^3 x 64, Ls = 16, reduced Ls),
+    # one timed solve each (too long for the headline's step count)
+    c4 = None
+    if cfg_name == "C3" and world == 1 and not args.no_c4:
+        c4 = config_record("C4", args, device, flush, barrier, maxall, rank)
+
     if rank == 0:
         line = {"metric": "time-to-solution (s) MSPCG vs plain CG at equal FP64 residual",
                 "value": t_step, "unit": "s", "n_gpus": world, "steps": K, "warmup": W,
@@ -770,6 +831,8 @@ def main():
                 "speedup_vs_cg": (cg["seconds"] / t_step) if cg else None,
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
                 "roofline": roofline, "dslash": dslash, "cpu_baseline": cpu}
+        if c4 is not None:
+            line["c4"] = c4
         print(json.dumps(line), flush=True)
     rep.close()
 

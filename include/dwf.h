@@ -16,8 +16,8 @@
  *     ((s*(V/2) + lex/2)*4 + spin)*3 + colour, complex interleaved (re, im),
  *     over the sites of one parity.  Element type by precision:
  *       DWF_F64: double[2], DWF_F32: float[2], DWF_F16: IEEE half[2],
- *       DWF_BF16: bfloat16[2], DWF_FX16: float[2] (the fixed-point format is
- *       a device storage format only; it is exchanged as FP32).
+ *       DWF_BF16: bfloat16[2], DWF_FX16 and DWF_FX8: float[2] (the fixed-point
+ *       formats are device storage formats only; they are exchanged as FP32).
  *   - Gauge field (host, FP64): ((lex*4 + mu)*3 + row)*3 + col complex
  *     (double[2]); mu = x, y, z, t; links must be SU(3) to ~1e-14 (the device
  *     copies keep two rows and rebuild the third).
@@ -62,7 +62,12 @@ typedef enum {
  * int16 integers q with one FP32 number, value = q / 32767 * max|component|
  * (the FP32 number kept is max/32767); loads unpack to FP32 and all
  * arithmetic is FP32, the fifth-dimension products on the tensor cores. */
-typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2, DWF_BF16 = 3, DWF_FX16 = 4 } dwf_prec;
+/* DWF_FX8: the 8-bit fixed-point format of the same section: 24 int8 integers
+ * per colour-spinor with one FP32 number, value = q / 127 * max|component|
+ * (the FP32 number kept is max/127), stored as three 8-byte chunks per 5D site.
+ * Like DWF_FX16 it is exchanged as FP32 and computed in FP32; its stages load
+ * neighbours directly (gather 0 only). */
+typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2, DWF_BF16 = 3, DWF_FX16 = 4, DWF_FX8 = 5 } dwf_prec;
 
 typedef enum {
     DWF_OP_D = 0,           /* D = 1 - M5^-1 M4_eo M5^-1 M4_oe (Sec. 2.2, Eq. dirac_equation) */
@@ -81,8 +86,8 @@ typedef struct {
     dwf_prec outer_prec;   /* outer vectors: DWF_F64, DWF_F32, or DWF_F16 / DWF_BF16 / DWF_FX16 (16-bit
                               iterations as in Sec. 3.2; the solution increment stays FP32);
                               below FP64 with FP64 reliable updates */
-    dwf_prec inner_prec;   /* DWF_F32, DWF_F16, DWF_BF16 or DWF_FX16 storage for the inner
-                              solves */
+    dwf_prec inner_prec;   /* DWF_F32, DWF_F16, DWF_BF16, DWF_FX16 or DWF_FX8 storage for the
+                              inner solves */
     double delta;          /* reliable update when ||r|| < delta * max ||r|| since the last one */
     int use_reduced_ls;    /* 1: reduced-Ls preconditioner (dwf_set_reduced_ls first) */
     int use_graph;         /* 1: capture each outer iteration in a CUDA graph */
@@ -229,6 +234,26 @@ dwf_status dwf_apply_T(dwf_handle *h, double *out_dev, const double *in_dev, con
                        int Ls_hat, int dagger);
 dwf_status dwf_T_contract(dwf_handle *h, double *G_host, const double *a_dev, int La, const double *b_dev,
                           int Lb);
+
+/* Vector arithmetic on canonical even-checkerboard fields of this handle's
+ * lattice with Ls slices (0 = the handle's Ls), for callers that assemble
+ * the method's outer loops (the transform training of Sec. 3.3) from the
+ * library's operators.  Fields are device arrays of complex numbers, FP64
+ * (DWF_F64) or FP32 (DWF_F32); both calls synchronise the handle's stream.
+ *
+ * dwf_field_axpby: out = a x + b y element by element, with the complex
+ * coefficients a = (a_re, a_im), b = (b_re, b_im); x and y (y may be NULL:
+ * out = a x, which with a = 1 converts between the precisions) in in_prec,
+ * out in out_prec; out may be x or y when the precisions agree.
+ *
+ * dwf_field_dot: result_host[0] + i result_host[1] = sum conj(a_e) b_e,
+ * accumulated in FP64 in a fixed order (the same inputs always give the same
+ * bits).  DWF_EINVAL for null pointers or other precisions. */
+dwf_status dwf_field_axpby(dwf_handle *h, void *out_dev, dwf_prec out_prec, double a_re, double a_im,
+                           const void *x_dev, double b_re, double b_im, const void *y_dev, dwf_prec in_prec,
+                           int Ls);
+dwf_status dwf_field_dot(dwf_handle *h, double *result_host, const void *a_dev, const void *b_dev, dwf_prec prec,
+                         int Ls);
 
 /* Ablation of the snake terms (Sec. 2.3, Eq. (eq:diri)): with on != 0 every
  * later use of the local operator A_s on this handle (dwf_apply with

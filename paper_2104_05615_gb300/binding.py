@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libdwf_gb300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "dwf.h")
 
 DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ECUDA, DWF_ENOCONV, DWF_ETIMEOUT, DWF_EUNSUPPORTED = range(7)
-DWF_F64, DWF_F32, DWF_F16, DWF_BF16, DWF_FX16 = range(5)
+DWF_F64, DWF_F32, DWF_F16, DWF_BF16, DWF_FX16, DWF_FX8 = range(6)
 DWF_OP_D, DWF_OP_DDAG, DWF_OP_DDAGD, DWF_OP_LOCAL_DDAGD, DWF_OP_M5INV, DWF_OP_M5INVDAG = range(6)
 
 
@@ -100,6 +100,8 @@ def lib() -> C.CDLL:
             "dwf_fma_peak": (i, [vp, i, C.POINTER(C.c_double)]),
             "dwf_query_geometry": (i, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(dwf_geometry)]),
             "dwf_set_wait_policy": (i, [vp, C.c_longlong, i]),
+            "dwf_field_axpby": (i, [vp, vp, i, d, d, vp, d, d, vp, i, i]),
+            "dwf_field_dot": (i, [vp, C.POINTER(C.c_double), vp, vp, i, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -322,6 +324,21 @@ def dwf_set_wait_policy(h, max_polls=0, force_timeout=False):
     """Poll limit of the bounded device waits (0: default) and the test-only
     forced time-out of the bulk-copy stage kernels."""
     return check(lib().dwf_set_wait_policy(h, int(max_polls), int(bool(force_timeout))), h)
+
+
+def dwf_field_axpby(h, out, out_prec, a, x, b=0.0, y=None, in_prec=None, Ls=0):
+    """out = a x + b y on canonical device fields (complex a, b; y None: a x)."""
+    a, b = complex(a), complex(b)
+    in_prec = out_prec if in_prec is None else in_prec
+    return check(lib().dwf_field_axpby(h, _ptr(out), int(out_prec), a.real, a.imag, _ptr(x), b.real, b.imag,
+                                       _ptr(y), int(in_prec), int(Ls)), h)
+
+
+def dwf_field_dot(h, a, b, prec, Ls=0):
+    """<a, b> = sum conj(a) b of canonical device fields, FP64, fixed-order sums."""
+    r = (C.c_double * 2)()
+    check(lib().dwf_field_dot(h, r, _ptr(a), _ptr(b), int(prec), int(Ls)), h)
+    return complex(r[0], r[1])
 
 
 def dwf_kernel_launch_count():

@@ -171,7 +171,7 @@ dwf_status dwf_query_geometry(const int dims[4], const int subdomain[4], dwf_geo
     return DWF_OK;
 }
 
-static bool prec_ok(int p) { return p >= DWF_F64 && p <= DWF_FX16; }
+static bool prec_ok(int p) { return p >= DWF_F64 && p <= DWF_FX8; }
 
 dwf_status dwf_pack(dwf_handle *h, void *packed, const void *canon, dwf_prec prec, void *stream)
 {
@@ -384,6 +384,35 @@ dwf_status dwf_T_contract(dwf_handle *h, double *G_host, const double *a, int La
         const LatticeGeom &g = *E.sys[0].g;
         launch_tcontract(Gd, a, La, b, Lb, g.Vh, work, E.st);
         DWF_CUDA(cudaMemcpyAsync(G_host, Gd, nG * sizeof(double), cudaMemcpyDeviceToHost, E.st));
+        DWF_CUDA(cudaStreamSynchronize(E.st));
+        return DWF_OK;
+    });
+}
+
+static bool field_prec(int p) { return p == DWF_F64 || p == DWF_F32; }
+
+dwf_status dwf_field_axpby(dwf_handle *h, void *out, dwf_prec out_prec, double a_re, double a_im, const void *x,
+                           double b_re, double b_im, const void *y, dwf_prec in_prec, int Ls)
+{
+    if (!h || !out || !x || !field_prec(out_prec) || !field_prec(in_prec) || Ls < 0 || Ls > 32) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        const long n = (long)dwf_field_elems(h, Ls);
+        launch_field_axpby(out, (Prec)out_prec, x, y, (Prec)in_prec, a_re, a_im, b_re, b_im, n, h->E->st);
+        DWF_CUDA(cudaStreamSynchronize(h->E->st));
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_field_dot(dwf_handle *h, double *result_host, const void *a, const void *b, dwf_prec prec, int Ls)
+{
+    if (!h || !result_host || !a || !b || !field_prec(prec) || Ls < 0 || Ls > 32) return DWF_EINVAL;
+    return guarded(&h->err, [&]() {
+        Engine &E = *h->E;
+        const long n = (long)dwf_field_elems(h, Ls);
+        void *work = E.ws("field_dot_work", field_dot_workspace_bytes());
+        double *res = (double *)E.ws("field_dot_result", 2 * sizeof(double));
+        launch_field_dot(res, a, b, (Prec)prec, n, work, E.st);
+        DWF_CUDA(cudaMemcpyAsync(result_host, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, E.st));
         DWF_CUDA(cudaStreamSynchronize(E.st));
         return DWF_OK;
     });

@@ -3,6 +3,7 @@
 // system) partial sums, precision conversion, canonical <-> packed layout,
 // the per-segment scalar recurrences of CG, and the reduced-Ls transform
 // z = T^+ zhat + mu r of Sec. 3.3.
+#include <algorithm>
 #include <atomic>
 #include <stdexcept>
 
@@ -47,6 +48,12 @@ __device__ __forceinline__ void load_any(Prec p, const void *base, long nsite, l
 #pragma unroll
         for (int r = 0; r < 24; r++) v[r] = (R)t[r];
     } break;
+    case PFX8: {
+        float t[24];
+        load_sp<TFX8>(base, nsite, site, s, Ls, t);
+#pragma unroll
+        for (int r = 0; r < 24; r++) v[r] = (R)t[r];
+    } break;
     default: {
         float t[24];
         load_sp<TBF16>(base, nsite, site, s, Ls, t);
@@ -84,6 +91,12 @@ __device__ __forceinline__ void store_any(Prec p, void *base, long nsite, long s
 #pragma unroll
         for (int r = 0; r < 24; r++) t[r] = (float)v[r];
         store_sp<TFX16>(base, nsite, site, s, Ls, t);
+    } break;
+    case PFX8: {
+        float t[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) t[r] = (float)v[r];
+        store_sp<TFX8>(base, nsite, site, s, Ls, t);
     } break;
     default: {
         float t[24];
@@ -380,7 +393,8 @@ __device__ __forceinline__ void load_canon(Prec p, const void *base, long Vh, lo
         for (int r = 0; r < 24; r++) v[r] = (R)q[r];
     } break;
     case P32:
-    case PFX16: {  // fixed-point fields are exchanged as FP32
+    case PFX16:
+    case PFX8: {  // fixed-point fields are exchanged as FP32
         const float *q = reinterpret_cast<const float *>(base) + off;
         for (int r = 0; r < 24; r++) v[r] = (R)q[r];
     } break;
@@ -405,7 +419,8 @@ __device__ __forceinline__ void store_canon(Prec p, void *base, long Vh, long cb
         for (int r = 0; r < 24; r++) q[r] = (double)v[r];
     } break;
     case P32:
-    case PFX16: {
+    case PFX16:
+    case PFX8: {
         float *q = reinterpret_cast<float *>(base) + off;
         for (int r = 0; r < 24; r++) q[r] = (float)v[r];
     } break;
@@ -708,6 +723,107 @@ void launch_tcontract(double *G_dev, const double *a, int La, const double *b, i
     DWF_CUDA(cudaGetLastError());
     tcontract_reduce<<<(npair + 255) / 256, 256, 0, st>>>(part, kContractCtas, npair,
                                                           reinterpret_cast<double2 *>(G_dev));
+    DWF_CUDA(cudaGetLastError());
+    count_launch(2);
+}
+
+}  // namespace dwf
+
+namespace dwf {
+
+// ------------------------------------------- canonical-field axpby and dot
+// out = a x + b y on canonical complex fields of n elements (x, y in pin,
+// out in pout: FP64 or FP32 complex); y null: out = a x (a cast for a = 1).
+template <typename TO, typename TI>
+__global__ void field_axpby_kernel(TO *out, const TI *x, const TI *y, double ar, double ai, double br, double bi,
+                                   long n)
+{
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const double xr = (double)x[2 * e], xi = (double)x[2 * e + 1];
+        double r = ar * xr - ai * xi, i = ar * xi + ai * xr;
+        if (y) {
+            const double yr = (double)y[2 * e], yi = (double)y[2 * e + 1];
+            r += br * yr - bi * yi;
+            i += br * yi + bi * yr;
+        }
+        out[2 * e] = (TO)r;
+        out[2 * e + 1] = (TO)i;
+    }
+}
+
+void launch_field_axpby(void *out, Prec pout, const void *x, const void *y, Prec pin, double ar, double ai,
+                        double br, double bi, long n, cudaStream_t st)
+{
+    const int nthr = 256;
+    const unsigned nblk = (unsigned)std::min<long>((n + nthr - 1) / nthr, 152L * 16);
+    if (nblk == 0) return;
+    if (pout == P64 && pin == P64)
+        field_axpby_kernel<double, double><<<nblk, nthr, 0, st>>>((double *)out, (const double *)x,
+                                                                 (const double *)y, ar, ai, br, bi, n);
+    else if (pout == P64)
+        field_axpby_kernel<double, float><<<nblk, nthr, 0, st>>>((double *)out, (const float *)x,
+                                                                (const float *)y, ar, ai, br, bi, n);
+    else if (pin == P64)
+        field_axpby_kernel<float, double><<<nblk, nthr, 0, st>>>((float *)out, (const double *)x,
+                                                                (const double *)y, ar, ai, br, bi, n);
+    else
+        field_axpby_kernel<float, float><<<nblk, nthr, 0, st>>>((float *)out, (const float *)x,
+                                                               (const float *)y, ar, ai, br, bi, n);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// <a, b> = sum conj(a_e) b_e in FP64: a fixed grid of CTAs, each thread a
+// fixed stride of elements, per-CTA partials summed by one CTA in a fixed
+// order, so the result does not depend on scheduling.
+constexpr int kDotCtas = 304, kDotThreads = 256;
+
+template <typename TI>
+__global__ void __launch_bounds__(kDotThreads) field_dot_kernel(const TI *a, const TI *b, long n, double2 *part)
+{
+    double r = 0.0, i = 0.0;
+    for (long e = (long)blockIdx.x * kDotThreads + threadIdx.x; e < n; e += (long)kDotCtas * kDotThreads) {
+        const double ar = (double)a[2 * e], ai = (double)a[2 * e + 1];
+        const double br = (double)b[2 * e], bi = (double)b[2 * e + 1];
+        r += ar * br + ai * bi;
+        i += ar * bi - ai * br;
+    }
+    __shared__ double sr[kDotThreads], si[kDotThreads];
+    sr[threadIdx.x] = r;
+    si[threadIdx.x] = i;
+    __syncthreads();
+    for (int o = kDotThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sr[threadIdx.x] += sr[threadIdx.x + o];
+            si[threadIdx.x] += si[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr[0], si[0]);
+}
+
+__global__ void field_dot_reduce(const double2 *part, double2 *out)
+{
+    if (threadIdx.x != 0) return;
+    double r = 0.0, i = 0.0;
+    for (int k = 0; k < kDotCtas; k++) {
+        r += part[k].x;
+        i += part[k].y;
+    }
+    *out = make_double2(r, i);
+}
+
+size_t field_dot_workspace_bytes() { return (kDotCtas + 1) * sizeof(double2); }
+
+void launch_field_dot(double *out_dev, const void *a, const void *b, Prec p, long n, void *work, cudaStream_t st)
+{
+    double2 *part = reinterpret_cast<double2 *>(work);
+    if (p == P64)
+        field_dot_kernel<double><<<kDotCtas, kDotThreads, 0, st>>>((const double *)a, (const double *)b, n, part);
+    else
+        field_dot_kernel<float><<<kDotCtas, kDotThreads, 0, st>>>((const float *)a, (const float *)b, n, part);
+    DWF_CUDA(cudaGetLastError());
+    field_dot_reduce<<<1, 32, 0, st>>>(part, reinterpret_cast<double2 *>(out_dev));
     DWF_CUDA(cudaGetLastError());
     count_launch(2);
 }

@@ -36,17 +36,30 @@ struct TFX16 {
     static constexpr Prec P = PFX16;
 };
 constexpr float kFx16Max = 32767.f;
+// 8-bit fixed point (Sec. 3.2, the paper's narrower fixed-point format): each
+// real an int8, one FP32 scale per colour-spinor (stored max|v| / 127); the 24
+// bytes of a (site, s) are three 8-byte chunks laid out [site][chunk][s][8 B],
+// so a warp running over s still reads contiguous words
+struct TFX8 {
+    using R = float;
+    static constexpr int NC = 3;
+    static constexpr Prec P = PFX8;
+};
+constexpr float kFx8Max = 127.f;
+
+// bytes of stored values per 5D site before the scale array
+template <class T> __host__ __device__ constexpr int data_bytes() { return T::P == PFX8 ? 24 : 48; }
 
 template <class T>
 __device__ __forceinline__ const float *scale_ptr(const void *base, long nsite, int Ls)
 {
     return reinterpret_cast<const float *>(reinterpret_cast<const char *>(base) +
-                                           (size_t)nsite * Ls * 48);
+                                           (size_t)nsite * Ls * data_bytes<T>());
 }
 template <class T>
 __device__ __forceinline__ float *scale_ptr(void *base, long nsite, int Ls)
 {
-    return reinterpret_cast<float *>(reinterpret_cast<char *>(base) + (size_t)nsite * Ls * 48);
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(base) + (size_t)nsite * Ls * data_bytes<T>());
 }
 
 __device__ __forceinline__ void unpack8(const uint4 &u, float *v, __half)
@@ -159,6 +172,48 @@ __device__ __forceinline__ uint4 pack8_fx16(const float *v, float inv)
                            __float_as_uint(fmaf(v[2 * i + 1], inv, kRound)), 0x5410);
     return make_uint4(q[0], q[1], q[2], q[3]);
 }
+// eight int8 of an 8-byte chunk to floats by bit placement: with its sign
+// bit flipped an int8 q reads as the unsigned q + 128, and the float whose
+// bits are 0x4B000000 | (q + 128) is 2^23 + 128 + q exactly
+constexpr float kFx8Bias = 8388736.f;  // 2^23 + 128
+__device__ __forceinline__ void unpack8_fx8(const uint2 &u, float *v)
+{
+    const uint32_t w[2] = {u.x ^ 0x80808080u, u.y ^ 0x80808080u};
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+            v[4 * i + b] = __uint_as_float(__byte_perm(w[i], 0x4B000000u, 0x7540u + b)) - kFx8Bias;
+}
+// eight floats times inv, each product within +-127 (to a few ulp), rounded
+// once to the nearest int8 (ties to even) by the fused v * inv + 1.5 * 2^23,
+// whose lowest byte is the integer in two's complement
+__device__ __forceinline__ uint2 pack8_fx8(const float *v, float inv)
+{
+    constexpr float kRound = 12582912.f;  // 1.5 * 2^23
+    uint32_t w[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const uint32_t f0 = __float_as_uint(fmaf(v[4 * i], inv, kRound));
+        const uint32_t f1 = __float_as_uint(fmaf(v[4 * i + 1], inv, kRound));
+        const uint32_t f2 = __float_as_uint(fmaf(v[4 * i + 2], inv, kRound));
+        const uint32_t f3 = __float_as_uint(fmaf(v[4 * i + 3], inv, kRound));
+        w[i] = __byte_perm(__byte_perm(f0, f1, 0x0040u), __byte_perm(f2, f3, 0x0040u), 0x5410u);
+    }
+    return make_uint2(w[0], w[1]);
+}
+template <>
+__device__ __forceinline__ void load_sp<TFX8>(const void *base, long nsite, long site, int s, int Ls,
+                                              float *v)
+{
+    const uint2 *p = reinterpret_cast<const uint2 *>(base) + (size_t)site * 3 * Ls + s;
+#pragma unroll
+    for (int c = 0; c < 3; c++) unpack8_fx8(__ldg(p + (size_t)c * Ls), v + 8 * c);
+    const float sc = __ldg(scale_ptr<TFX8>(base, nsite, Ls) + (size_t)site * Ls + s);
+#pragma unroll
+    for (int i = 0; i < 24; i++) v[i] *= sc;
+}
+
 template <>
 __device__ __forceinline__ void load_sp<TFX16>(const void *base, long nsite, long site, int s,
                                                int Ls, float *v)
@@ -252,11 +307,38 @@ __device__ __forceinline__ void store_sp<TFX16>(void *base, long nsite, long sit
     store_fx16(base, nsite, site, s, Ls, v, 1.f);
 }
 
+// 8-bit fixed-point store of v with the stored scale multiplied by f
+__device__ __forceinline__ void store_fx8(void *base, long nsite, long site, int s, int Ls,
+                                          const float *v, float f)
+{
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
+    const float sc = m > 0.f ? m / kFx8Max : 1.f;
+    const float inv = m > 0.f ? kFx8Max / m : 0.f;
+    uint2 *p = reinterpret_cast<uint2 *>(base) + (size_t)site * 3 * Ls + s;
+#pragma unroll
+    for (int c = 0; c < 3; c++) p[(size_t)c * Ls] = pack8_fx8(v + 8 * c, inv);
+    scale_ptr<TFX8>(base, nsite, Ls)[(size_t)site * Ls + s] = sc * f;
+}
+template <>
+__device__ __forceinline__ void store_sp<TFX8>(void *base, long nsite, long site, int s, int Ls,
+                                               const float *v)
+{
+    store_fx8(base, nsite, site, s, Ls, v, 1.f);
+}
+
 // Scaled 16-bit store of v * f (FP16 or 16-bit fixed point): the values are
 // normalised by max|v| and the factor goes into the stored scale only.
 template <class T>
 __device__ __forceinline__ void store_sp_scaled(void *base, long nsite, long site, int s, int Ls,
                                                 const float *v, float f);
+template <>
+__device__ __forceinline__ void store_sp_scaled<TFX8>(void *base, long nsite, long site, int s, int Ls,
+                                                      const float *v, float f)
+{
+    store_fx8(base, nsite, site, s, Ls, v, f);
+}
 template <>
 __device__ __forceinline__ void store_sp_scaled<TFX16>(void *base, long nsite, long site, int s, int Ls,
                                                        const float *v, float f)
@@ -343,6 +425,11 @@ __device__ __forceinline__ void load_link12<TBF16>(const void *links, long row, 
 }
 template <>
 __device__ __forceinline__ void load_link12<TFX16>(const void *links, long row, int k, float *u)
+{
+    load_link12_half(links, row, k, u);
+}
+template <>
+__device__ __forceinline__ void load_link12<TFX8>(const void *links, long row, int k, float *u)
 {
     load_link12_half(links, row, k, u);
 }

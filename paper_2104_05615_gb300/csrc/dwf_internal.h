@@ -21,27 +21,29 @@
 
 namespace dwf {
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PFX16 = 4 };
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PFX16 = 4, PFX8 = 5 };
+constexpr int kNumPrec = 6;
 // formats stored with one FP32 scale per (site, s) after the data
-inline bool scaled_format(Prec p) { return p == P16 || p == PFX16; }
+inline bool scaled_format(Prec p) { return p == P16 || p == PFX16 || p == PFX8; }
 
 constexpr int kSegPad = 32;  // every segment (block / system) is padded to this many sites
 
-inline int elem_bytes(Prec p) { return p == P64 ? 8 : p == P32 ? 4 : 2; }
+inline int elem_bytes(Prec p) { return p == P64 ? 8 : p == P32 ? 4 : p == PFX8 ? 1 : 2; }
 inline size_t field_bytes(Prec p, long nsite, int Ls)
 {
     size_t b = (size_t)nsite * Ls * 24 * elem_bytes(p);
     if (scaled_format(p)) b += (size_t)nsite * Ls * sizeof(float);
     return b;
 }
-// scale array of an FP16 field sits right after its data
+// scale array of a scaled field sits right after its data
 inline float *field_scale(void *data, Prec p, long nsite, int Ls)
 {
-    return scaled_format(p) ? (float *)((char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
+    return scaled_format(p) ? (float *)((char *)data + (size_t)nsite * Ls * 24 * elem_bytes(p)) : nullptr;
 }
 inline const float *field_scale(const void *data, Prec p, long nsite, int Ls)
 {
-    return scaled_format(p) ? (const float *)((const char *)data + (size_t)nsite * Ls * 24 * 2) : nullptr;
+    return scaled_format(p) ? (const float *)((const char *)data + (size_t)nsite * Ls * 24 * elem_bytes(p))
+                            : nullptr;
 }
 
 // One stage of an operator: out = Epilogue(F . hop(G . in)), see stage.cu.
@@ -179,6 +181,14 @@ void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, i
 size_t tcontract_workspace_bytes(int La, int Lb);
 void launch_tcontract(double *G_dev, const double *a, int La, const double *b, int Lb, long Vh,
                       void *work, cudaStream_t st);
+
+// Canonical complex fields of n elements (FP64 or FP32): out = a x + b y
+// (y null: out = a x) and <a, b> into out_dev[2] (FP64, fixed-order sums;
+// work: field_dot_workspace_bytes()).
+void launch_field_axpby(void *out, Prec pout, const void *x, const void *y, Prec pin, double ar, double ai,
+                        double br, double bi, long n, cudaStream_t st);
+size_t field_dot_workspace_bytes();
+void launch_field_dot(double *out_dev, const void *a, const void *b, Prec p, long n, void *work, cudaStream_t st);
 
 // Process-wide launch counter (every launch_* adds its kernels).
 void count_launch(long long n = 1);

@@ -451,7 +451,7 @@ static const void *matp(const Mats &m, MatKind k, Prec p)
     return p == P64 ? (const void *)m.d64[k] : (const void *)m.d32[k];
 }
 
-static bool is_half(Prec p) { return p == P16 || p == PB16 || p == PFX16; }
+static bool is_half(Prec p) { return p == P16 || p == PB16 || p == PFX16 || p == PFX8; }
 
 // Matrices of a stage: CUDA-core path F (and G), tensor-core path the fused
 // operand A; G is kept non-null on the tensor-core path only as a flag.
@@ -514,7 +514,7 @@ void Engine::autotune(Prec p, int which, int Ls_op, int reps)
     EventPair ev;
     std::vector<KCfg> cand;
     const int tiles[] = {4, 8, 16, 32};
-    const int ngather = p == P64 ? 1 : (p == P32 ? 2 : 3);
+    const int ngather = (p == P64 || p == PFX8) ? 1 : (p == P32 ? 2 : 3);
     for (int gather = 0; gather < ngather; gather++)
         for (int tile : tiles) {
             if (!stage_fits(p, tile, Ls_op, gather)) continue;

@@ -173,7 +173,7 @@ class Engine {
         int gather = 0;
         bool tuned = false;
     };
-    KCfg cfg[2][5];  // [local|global][Prec]
+    KCfg cfg[2][kNumPrec];  // [global|local][Prec]
     bool autotune_on = true;
     // Times every fitting (tile, gather) candidate on this engine's lattice
     // and keeps the fastest; `which` 0 global, 1 local at fifth extent Ls_op.

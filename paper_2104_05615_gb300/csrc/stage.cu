@@ -10,6 +10,7 @@ extern template void launch_stage_prec<TF32>(StageMode, bool, const StageArgs &,
 extern template void launch_stage_prec<TF16>(StageMode, bool, const StageArgs &, cudaStream_t);
 extern template void launch_stage_prec<TBF16>(StageMode, bool, const StageArgs &, cudaStream_t);
 extern template void launch_stage_prec<TFX16>(StageMode, bool, const StageArgs &, cudaStream_t);
+extern template void launch_stage_prec<TFX8>(StageMode, bool, const StageArgs &, cudaStream_t);
 extern template void launch_stage_tc<TF16>(StageMode, bool, const StageArgs &, cudaStream_t);
 extern template void launch_stage_tc<TBF16>(StageMode, bool, const StageArgs &, cudaStream_t);
 extern template void launch_stage_tc<TFX16>(StageMode, bool, const StageArgs &, cudaStream_t);
@@ -32,11 +33,15 @@ void launch_stage(Prec prec, StageMode mode, bool mphi_in, const StageArgs &a, c
     case P16: launch_stage_prec<TF16>(mode, mphi_in, a, st); break;
     case PB16: launch_stage_prec<TBF16>(mode, mphi_in, a, st); break;
     case PFX16: launch_stage_prec<TFX16>(mode, mphi_in, a, st); break;
+    case PFX8: launch_stage_prec<TFX8>(mode, mphi_in, a, st); break;
     }
 }
 
 bool stage_fits(Prec prec, int tile, int Ls, int gather)
 {
+    // the 8-bit format gathers directly (its 8-byte chunks have no bulk-copy
+    // or tensor-core-hop instance)
+    if (prec == PFX8 && gather != 0) return false;
     if (gather == 2) {
         // tensor-core hop: 16-bit storage, 8-site tiles, Ls in {4, 8, 12, 16}
         const bool half = prec == P16 || prec == PB16 || prec == PFX16;
@@ -47,7 +52,7 @@ bool stage_fits(Prec prec, int tile, int Ls, int gather)
     const int NC = prec == P64 ? 12 : prec == P32 ? 6 : 3;
     const int esz = prec == P64 ? 8 : prec == P32 ? 4 : 2;
     const int rsz = prec == P64 ? 8 : 4;
-    const bool tc = prec == P16 || prec == PB16 || prec == PFX16;
+    const bool tc = prec == P16 || prec == PB16 || prec == PFX16 || prec == PFX8;
     const bool tma = gather == 1 && prec != P64;
     const StageSmem L = stage_smem(tile, Ls, NC, esz, rsz, tma, tc, scaled_format(prec) && Ls % 4 == 0, true, true);
     const int nthr = (tile * Ls + 31) / 32 * 32;

@@ -509,12 +509,12 @@ template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS, int TS
 // 16-bit stages with precomputed M_phi input are held to 64 registers (two
 // 512-thread blocks' worth per SM): the occupancy gain outweighs the extra
 // rematerialisation.  (M_phi on load needs more live values.)
-__global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == PFX16) && !kMphi) ? 2 : 1)
+__global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8) && !kMphi) ? 2 : 1)
     stage_kernel(const StageArgs a)
 {
     using R = typename T::R;
-    constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16);
-    constexpr bool kScale = (T::P == P16 || T::P == PFX16);
+    constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8);
+    constexpr bool kScale = (T::P == P16 || T::P == PFX16 || T::P == PFX8);
     constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
     constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
     constexpr int NC = T::NC;
@@ -782,6 +782,27 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                                        reinterpret_cast<const __half2 *>(sU + (jl * 8 + k) * kLinkStride),
                                        __float2half2_rn(w), acc2);
                 return;
+            } else if constexpr (T::P == PFX8) {
+                // 8-bit fixed point: three 8-byte chunks per 5D site
+                const uint2 *gp = reinterpret_cast<const uint2 *>(a.in) + (size_t)idx * 3 * Ls;
+                const float *gs = scale_ptr<TFX8>(a.in, a.nin, Ls) + idx * Ls;
+                auto ld = [&](int ss, float *v) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) unpack8_fx8(__ldg(gp + (size_t)c * Ls + ss), v + 8 * c);
+                    return __ldg(gs + ss);
+                };
+                sc = ld(s, psi);
+                if (kMphi) {
+                    R q[24];
+                    const R c0 = cb * sc;
+                    const R fp = (s + 1 < Ls ? cc : cc * wm) * ld(sp, q);
+#pragma unroll
+                    for (int r = 0; r < 12; r++) psi[r] = c0 * psi[r] + fp * q[r];
+                    const R fm = (s > 0 ? cc : cc * wm) * ld(sm1, q);
+#pragma unroll
+                    for (int r = 12; r < 24; r++) psi[r] = c0 * psi[r] + fm * q[r];
+                    sc = 1;
+                }
             } else {
                 const uint4 *gp = reinterpret_cast<const uint4 *>(a.in) + (size_t)idx * NC * Ls;
                 uint4 raw[NC];
@@ -1187,13 +1208,13 @@ static void launch_t(const StageArgs &a, cudaStream_t st)
 {
     using R = typename T::R;
     using LE = typename LinkElem<T>::E;
-    constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16);
+    constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8);
     constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
     constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
     const int TS = a.tile, Ls = a.Ls;
     const int nthr = (TS * Ls + 31) / 32 * 32;
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
-    const bool scale_bulk = (T::P == P16 || T::P == PFX16) && (Ls % 4 == 0);
+    const bool scale_bulk = (T::P == P16 || T::P == PFX16 || T::P == PFX8) && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, T::NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
                                    has_dot, !kTC || kMode == MODE_S4);
     static bool attr_set = false;
@@ -1232,9 +1253,13 @@ static void dispatch_mode(StageMode mode, bool mphi, const StageArgs &a, cudaStr
 template <class T>
 void launch_stage_prec(StageMode mode, bool mphi, const StageArgs &a, cudaStream_t st)
 {
-    if (a.gather == 1 && T::P != P64) {
-        dispatch_mode<T, true, 0, 0>(mode, mphi, a, st);
-        return;
+    if constexpr (T::P != P64 && T::P != PFX8) {
+        if (a.gather == 1) {
+            dispatch_mode<T, true, 0, 0>(mode, mphi, a, st);
+            return;
+        }
+    } else {
+        if (a.gather == 1) throw std::runtime_error("no bulk-copy gather for this storage format");
     }
     if constexpr (T::P == P64) {
         // compile-time fifth extent for the reliable updates' common Ls

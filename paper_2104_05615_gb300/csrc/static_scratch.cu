@@ -62,7 +62,7 @@ extern "C" dwf_status dwf_apply_packed_static(dwf_handle *h, void *out, const vo
                                               dwf_op op, dwf_prec prec, void *stream)
 {
     using namespace dwf;
-    if (!h || !out || !in || out == in || prec < DWF_F64 || prec > DWF_FX16) return DWF_EINVAL;
+    if (!h || !out || !in || out == in || prec < DWF_F64 || prec > DWF_FX8) return DWF_EINVAL;
     if (op != DWF_OP_D && op != DWF_OP_DDAG && op != DWF_OP_DDAGD) {
         dwf_handle_set_error(h, "static-scratch apply supports D, D^+ and D^+D only");
         return DWF_EINVAL;

@@ -1,8 +1,8 @@
 """Convenience wrapper over the C ABI for one lattice, with torch device tensors.
 
 Canonical even/odd fields are torch tensors of shape (Ls, V/2, 4, 3):
-complex128 (FP64), complex64 (FP32 and the 16-bit fixed-point format, which
-is a device storage format exchanged as FP32); FP16 / BF16 fields carry a
+complex128 (FP64), complex64 (FP32 and the 16- and 8-bit fixed-point formats,
+device storage formats exchanged as FP32); FP16 / BF16 fields carry a
 trailing (re, im) axis: float16 / bfloat16 of shape (Ls, V/2, 4, 3, 2).
 """
 from __future__ import annotations
@@ -14,7 +14,7 @@ from . import binding as B
 from . import inputs
 
 PREC = {"f64": B.DWF_F64, "f32": B.DWF_F32, "f16": B.DWF_F16, "bf16": B.DWF_BF16,
-        "fx16": B.DWF_FX16}
+        "fx16": B.DWF_FX16, "fx8": B.DWF_FX8}
 OPS = {"D": B.DWF_OP_D, "Ddag": B.DWF_OP_DDAG, "DdagD": B.DWF_OP_DDAGD,
        "local": B.DWF_OP_LOCAL_DDAGD, "m5inv": B.DWF_OP_M5INV, "m5invdag": B.DWF_OP_M5INVDAG}
 
@@ -24,7 +24,7 @@ def to_device(x: np.ndarray, prec: str, device="cuda") -> torch.Tensor:
     t = torch.from_numpy(np.ascontiguousarray(x))
     if prec == "f64":
         return t.to(device)
-    if prec in ("f32", "fx16"):
+    if prec in ("f32", "fx16", "fx8"):
         return t.to(torch.complex64).to(device)
     r = torch.view_as_real(t.to(torch.complex64))
     return r.to(torch.float16 if prec == "f16" else torch.bfloat16).to(device).contiguous()
@@ -39,7 +39,7 @@ def to_numpy(t: torch.Tensor) -> np.ndarray:
 def empty_like_prec(shape, prec, device="cuda"):
     if prec == "f64":
         return torch.empty(shape, dtype=torch.complex128, device=device)
-    if prec in ("f32", "fx16"):
+    if prec in ("f32", "fx16", "fx8"):
         return torch.empty(shape, dtype=torch.complex64, device=device)
     return torch.empty(tuple(shape) + (2,), dtype=torch.float16 if prec == "f16" else torch.bfloat16,
                        device=device)

@@ -21,9 +21,12 @@ value).  Directions carry momentum (heavy ball, reset to steepest descent when
 not a descent direction).  Mhat^-1 is the blocks' inner CG run for a fixed,
 large number of iterations (the exact inverse the gradient assumes).
 
-The device backend calls the library (dwf_apply on the local operator,
-dwf_reduced_local_inverse, dwf_apply_T, dwf_T_contract); torch holds the
-fields and does the axpys and inner products.
+The device backend calls the library for every vector operation (dwf_apply
+on the local operator, dwf_reduced_local_inverse, dwf_apply_T,
+dwf_T_contract, dwf_field_axpby, dwf_field_dot); torch only holds the device
+fields.  What runs on the host is the parameters' own arithmetic: the
+(4 Ls_hat) x (4 Ls) matrices T, G and the direction, and the five
+coefficients of the line-search quartic.
 """
 from __future__ import annotations
 
@@ -47,8 +50,16 @@ class DeviceBackend:
         return self.torch.zeros((L,) + tuple(self.lat.shape[1:]), dtype=self.torch.complex128, device="cuda")
 
     def M(self, x):
-        dt = self.torch.complex64 if self.op_prec == "f32" else self.torch.complex128
-        return self.lat.apply("local", x.to(dt), self.op_prec).to(self.torch.complex128)
+        B = self.B
+        if self.op_prec == "f64":
+            return self.lat.apply("local", x.contiguous(), "f64")
+        # FP32 operator: the library converts in and out
+        xs = self.torch.empty(x.shape, dtype=self.torch.complex64, device="cuda")
+        B.dwf_field_axpby(self.lat.h, xs, B.DWF_F32, 1.0, x.contiguous(), in_prec=B.DWF_F64)
+        ys = self.lat.apply("local", xs, "f32")
+        out = self.zeros(x.shape[0])
+        B.dwf_field_axpby(self.lat.h, out, B.DWF_F64, 1.0, ys, in_prec=B.DWF_F32)
+        return out
 
     def Minv_hat(self, x):
         out = self.zeros(self.Lh)
@@ -64,7 +75,14 @@ class DeviceBackend:
         return self.B.dwf_T_contract(self.lat.h, a.contiguous(), a.shape[0], b.contiguous(), b.shape[0])
 
     def dot(self, a, b):
-        return complex(self.torch.vdot(a.reshape(-1), b.reshape(-1)).item())
+        return self.B.dwf_field_dot(self.lat.h, a.contiguous(), b.contiguous(), self.B.DWF_F64, a.shape[0])
+
+    def axpby(self, a, x, b, y):
+        """a x + b y (a new field)."""
+        out = self.zeros(x.shape[0])
+        self.B.dwf_field_axpby(self.lat.h, out, self.B.DWF_F64, a, x.contiguous(), b, y.contiguous(),
+                               Ls=x.shape[0])
+        return out
 
 
 class TransformTrainer:
@@ -82,7 +100,7 @@ class TransformTrainer:
     def _e0(self, T, v):
         be = self.be
         w = be.Minv_hat(be.T(T, v))
-        return w, be.M(be.T(T, w, dagger=True) + self.mu * v) - v
+        return w, be.axpby(1.0, be.M(be.axpby(1.0, be.T(T, w, dagger=True), self.mu, v)), -1.0, v)
 
     def loss(self, T):
         """chi^2(T) / sum_i |v_i|^2."""
@@ -107,7 +125,7 @@ class TransformTrainer:
         for v in self.vs:
             w, e0 = self._e0(T, v)
             y = be.Minv_hat(be.T(D, v))
-            e1 = be.M(be.T(D, w, dagger=True) + be.T(T, y, dagger=True))
+            e1 = be.M(be.axpby(1.0, be.T(D, w, dagger=True), 1.0, be.T(T, y, dagger=True)))
             e2 = be.M(be.T(D, y, dagger=True))
             d00, d11, d22 = be.dot(e0, e0).real, be.dot(e1, e1).real, be.dot(e2, e2).real
             d01, d02, d12 = be.dot(e0, e1).real, be.dot(e0, e2).real, be.dot(e1, e2).real

@@ -50,6 +50,8 @@ def test_null_handle_is_rejected(lib):
         "dwf_set_kernel_config": (None, B.DWF_F32, 0, C.byref(kc)),
         "dwf_batch_mspcg": (None, None, None, C.byref(p), None, C.byref(st)),
         "dwf_set_wait_policy": (None, 0, 0),
+        "dwf_field_axpby": (None, None, B.DWF_F64, 1.0, 0.0, None, 0.0, 0.0, None, B.DWF_F64, 0),
+        "dwf_field_dot": (None, None, None, None, B.DWF_F64, 0),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == E, name

@@ -43,7 +43,7 @@ def test_mixed_cg_reliable_updates(orc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("inner", ["f32", "f16", "bf16", "fx16"])
+@pytest.mark.parametrize("inner", ["f32", "f16", "bf16", "fx16", "fx8"])
 def test_mspcg_converges_and_beats_cg(orc, inner):
     lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
     bd = torch.from_numpy(b).cuda()

@@ -32,6 +32,9 @@ class OracleBackend:
     def dot(self, a, b):
         return complex(np.vdot(a, b))
 
+    def axpby(self, a, x, b, y):
+        return a * x + b * y
+
 
 def _setup(orc, seed=3):
     U = inputs.gauge_field(DIMS, 0.5, 11)
