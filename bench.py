@@ -171,9 +171,10 @@ def setup(cfg_name, device):
     return cfg, lat, b, bd
 
 
-STAGE_SOURCES = ("stage_impl.cuh", "device_common.cuh", "dwf_internal.h", "stage.cu",
-                 "stage_f16.cu", "stage_f32.cu", "stage_bf16.cu", "stage_f64.cu", "stage_fx16.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_stage_kernels_16x16x16x32_Ls12.md")
+STAGE_SOURCES = ("stage_impl.cuh", "stage_tc.cuh", "device_common.cuh", "dwf_internal.h", "stage.cu",
+                 "stage_f16.cu", "stage_f32.cu", "stage_bf16.cu", "stage_f64.cu", "stage_fx16.cu",
+                 "stage_fx8.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_stage_kernels.md")
 
 
 def kernel_sources_sha1():
@@ -522,10 +523,17 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the record of the 32^3 x 64, Ls = 16 workload (one timed solve each)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "ops", "sample", "sweep", "waves", "inner", "train"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "ops", "sample", "sweep", "waves", "inner", "train", "apply"],
                     help="ops: only apply the operators (for profilers); inner: outer iterations "
                          "and time to solution against the inner iteration count and precision")
     ap.add_argument("--op-reps", type=int, default=3)
+    ap.add_argument("--op", default="local", choices=["local", "DdagD", "D", "Ddag"],
+                    help="apply mode: the operator applied")
+    ap.add_argument("--prec", default=None, help="apply mode: storage format (default: the workload's inner one)")
+    ap.add_argument("--lattice", default=None,
+                    help="apply mode: 'LXxLYxLZxLT,Ls,BXxBYxBZxBT' instead of the workload's lattice "
+                         "(links exp(0.6 i H), seed 103)")
     ap.add_argument("--kcfg", default=None,
                     help="fixed stage launch config 'tile,gather' for both operators (ops and solve modes)")
     ap.add_argument("--peaks", action="store_true",
@@ -570,6 +578,33 @@ def main():
     if cfg_name == "C5":
         run_batch(args, device, rank, world, barrier, maxall)
         rep.close()
+        return
+    if args.mode == "apply":
+        # one operator applied op_reps times in one storage format, with the
+        # launch shape fixed by --kcfg (for profilers: nothing is timed here)
+        from paper_2104_05615_gb300.lattice import Lattice, OPS, PREC, to_device
+        if args.lattice:
+            d, L, sb = args.lattice.split(",")
+            dims, Ls, sub = tuple(int(v) for v in d.split("x")), int(L), tuple(int(v) for v in sb.split("x"))
+            alat = Lattice(dims, Ls, 1.5, 0.5, 1.8, 0.002, inputs.gauge_field(dims, 0.6, 103), sub)
+        else:
+            cfg = inputs.CONFIGS[cfg_name]
+            dims, Ls = cfg["dims"], cfg["Ls"]
+            alat = Lattice.from_config(cfg)
+        prec = args.prec or inputs.CONFIGS[cfg_name].get("inner_prec", "f32")
+        if args.kcfg:
+            tile, gather = (int(v) for v in args.kcfg.split(","))
+            B.dwf_set_kernel_config(alat.h, PREC[prec], 1 if args.op == "local" else 0, tile, gather)
+        xin = alat.pack(to_device(inputs.gaussian_spinor_cb(dims, Ls, 5), prec), prec)
+        out = alat.packed(prec)
+        for _ in range(args.op_reps):
+            B.dwf_apply_packed(alat.h, out, xin, OPS[args.op], PREC[prec])
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"mode": "apply", "op": args.op, "prec": prec, "dims": list(dims), "Ls": Ls,
+                              "applications": args.op_reps,
+                              "kernel_config": B.dwf_get_kernel_config(alat.h, PREC[prec],
+                                                                       1 if args.op == "local" else 0)}))
         return
     cfg, lat, b, bd = setup(cfg_name, device)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)

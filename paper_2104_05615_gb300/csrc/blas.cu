@@ -309,18 +309,159 @@ static void launch_blas_t(BlasOp op, const BlasArgs &a, unsigned nblk, int nthr,
     }
 }
 
+// The same operations when every operand is FP32 (the outer iteration's
+// vectors): each operand is streamed one 16-byte chunk at a time (six per 5D
+// site), so only a few values are live per thread and more warps fit on an
+// SM, keeping more loads in flight.
+__device__ __forceinline__ float4 ld4(const void *base, long site, int c, int s, int Ls)
+{
+    return __ldg(reinterpret_cast<const float4 *>(base) + ((size_t)site * 6 + c) * Ls + s);
+}
+__device__ __forceinline__ void st4(void *base, long site, int c, int s, int Ls, float4 v)
+{
+    reinterpret_cast<float4 *>(base)[((size_t)site * 6 + c) * Ls + s] = v;
+}
+__device__ __forceinline__ float dot4(float4 x, float4 y) { return x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w; }
+__device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y)
+{
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+template <int OP>
+__global__ void __launch_bounds__(512, 3) blas32_kernel(BlasArgs a)
+{
+    const int Ls = a.Ls;
+    const int jl = threadIdx.x / Ls, s = threadIdx.x - jl * Ls;
+    const long i = a.site0 + (long)blockIdx.x * a.tile + jl;
+    const long cta = a.site0 / a.tile + blockIdx.x;
+    const bool active = jl < a.tile && i < (a.site_end ? a.site_end : a.nsite);
+    constexpr int ncomp = OP == BLAS_DOT2 ? 2 : 1;
+    const int seg = (active && a.tile_seg) ? a.tile_seg[i / kSegPad] : 0;
+    if (a.active) {
+        const long i0 = a.site0 + (long)blockIdx.x * a.tile;
+        const int sys = a.tile_sys ? a.tile_sys[i0 / kSegPad] : 0;
+        if (!a.active[sys]) {
+            if (a.part && threadIdx.x == 0)
+                for (int c = 0; c < ncomp; c++) a.part[(size_t)cta * ncomp + c] = 0.0;
+            return;
+        }
+    }
+    extern __shared__ __align__(16) unsigned char blas_smem[];
+    float4 *sv = reinterpret_cast<float4 *>(blas_smem);  // [site][s][chunk] (M_phi output)
+    float d0 = 0.f, d1 = 0.f;
+    if (active) {
+        if constexpr (OP == BLAS_DOT || OP == BLAS_DOT2) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const float4 x = ld4(a.v[0], i, c, s, Ls);
+                d0 += dot4(x, ld4(a.v[1], i, c, s, Ls));
+                if constexpr (OP == BLAS_DOT2) d1 += dot4(x, ld4(a.v[2], i, c, s, Ls));
+            }
+        } else if constexpr (OP == BLAS_NORM2) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const float4 x = ld4(a.v[0], i, c, s, Ls);
+                d0 += dot4(x, x);
+            }
+        } else if constexpr (OP == BLAS_CG_UPDATE) {
+            // x += alpha p ; r -= alpha Ap ; |r|^2
+            const float al = (float)(a.scal[0][seg] * a.scal_sign[0]);
+            void *xo = a.v[4] ? a.v[4] : a.v[0];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const float4 x = a.x_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(a.v[0], i, c, s, Ls);
+                st4(xo, i, c, s, Ls, axpy4(al, ld4(a.v[1], i, c, s, Ls), x));
+            }
+            if (a.v[2]) {
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    const float4 r = axpy4(-al, ld4(a.v[3], i, c, s, Ls), ld4(a.v[2], i, c, s, Ls));
+                    st4(a.v[2], i, c, s, Ls, r);
+                    d0 += dot4(r, r);
+                }
+            }
+        } else if constexpr (OP == BLAS_XPAY) {
+            // v0 = v1 + beta v0
+            const float be = (float)(a.scal[0][seg] * a.scal_sign[0]);
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const float4 v = axpy4(be, ld4(a.v[0], i, c, s, Ls), ld4(a.v[1], i, c, s, Ls));
+                st4(a.v[0], i, c, s, Ls, v);
+                if (a.mphi_out) sv[(jl * Ls + s) * 6 + c] = v;
+            }
+        } else if constexpr (OP == BLAS_AXPY_ZERO) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) st4(a.v[0], i, c, s, Ls, make_float4(0.f, 0.f, 0.f, 0.f));
+        } else if constexpr (OP == BLAS_COPY) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const float4 v = ld4(a.v[1], i, c, s, Ls);
+                st4(a.v[0], i, c, s, Ls, v);
+                if (a.v[2]) st4(a.v[2], i, c, s, Ls, v);
+                if (a.mphi_out) sv[(jl * Ls + s) * 6 + c] = v;
+                d0 += dot4(v, v);
+            }
+        }
+    }
+    if constexpr (OP == BLAS_COPY || OP == BLAS_XPAY) {
+        if (a.mphi_out) {
+            // u = M_phi v: (M_phi v)_s = -(b v_s + c (P_- v_{s+1} + P_+ v_{s-1}))/2,
+            // wrap terms times -mass; chunks 0..2 hold spins 0, 1 (P_-), 3..5 spins 2, 3
+            __syncthreads();
+            if (active) {
+                const int sys = a.tile_sys ? a.tile_sys[i / kSegPad] : 0;
+                const double *mp = a.mphi + 5 * sys;
+                const float cb = (float)(-0.5 * mp[0]), cc = (float)(-0.5 * mp[1]), wm = (float)(-mp[2]);
+                const int sp = s + 1 < Ls ? s + 1 : 0, sm = s > 0 ? s - 1 : Ls - 1;
+                const float fp = s + 1 < Ls ? cc : cc * wm, fm = s > 0 ? cc : cc * wm;
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    const float4 v = sv[(jl * Ls + s) * 6 + c];
+                    const float4 w = sv[(jl * Ls + (c < 3 ? sp : sm)) * 6 + c];
+                    const float f = c < 3 ? fp : fm;
+                    st4(a.mphi_out, i, c, s, Ls,
+                        make_float4(cb * v.x + f * w.x, cb * v.y + f * w.y, cb * v.z + f * w.z, cb * v.w + f * w.w));
+                }
+            }
+        }
+    }
+    if (a.part) block_reduce_store((double)d0, (double)d1, ncomp, a.part, cta);
+}
+
+template <int OP>
+static void launch_b32(const BlasArgs &a, unsigned nblk, int nthr, size_t sm, cudaStream_t st)
+{
+    blas32_kernel<OP><<<nblk, nthr, sm, st>>>(a);
+}
+
 void launch_blas(BlasOp op, const BlasArgs &a, cudaStream_t st)
 {
     if (a.nsite == 0) return;
-    bool dbl = false;
-    for (int k = 0; k < 5; k++)
+    bool dbl = false, all32 = op != BLAS_RESIDUAL && (!a.mphi_out || a.mphi_prec == P32);
+    for (int k = 0; k < 5; k++) {
         if (a.v[k] && a.p[k] == P64) dbl = true;
+        if (a.v[k] && a.p[k] != P32) all32 = false;
+    }
     const int nthr = a.tile * a.Ls;
     const long end = a.site_end ? a.site_end : a.nsite;
     const unsigned nblk = (unsigned)((end - a.site0 + a.tile - 1) / a.tile);
     const size_t sm = a.mphi_out ? (size_t)nthr * 24 * (dbl ? 8 : 4) : 0;
-    if (dbl) launch_blas_t<double>(op, a, nblk, nthr, sm, st);
-    else launch_blas_t<float>(op, a, nblk, nthr, sm, st);
+    if (all32) {
+        switch (op) {
+        case BLAS_DOT: launch_b32<BLAS_DOT>(a, nblk, nthr, sm, st); break;
+        case BLAS_NORM2: launch_b32<BLAS_NORM2>(a, nblk, nthr, sm, st); break;
+        case BLAS_CG_UPDATE: launch_b32<BLAS_CG_UPDATE>(a, nblk, nthr, sm, st); break;
+        case BLAS_XPAY: launch_b32<BLAS_XPAY>(a, nblk, nthr, sm, st); break;
+        case BLAS_AXPY_ZERO: launch_b32<BLAS_AXPY_ZERO>(a, nblk, nthr, sm, st); break;
+        case BLAS_COPY: launch_b32<BLAS_COPY>(a, nblk, nthr, sm, st); break;
+        case BLAS_DOT2: launch_b32<BLAS_DOT2>(a, nblk, nthr, sm, st); break;
+        default: break;
+        }
+    } else if (dbl) {
+        launch_blas_t<double>(op, a, nblk, nthr, sm, st);
+    } else {
+        launch_blas_t<float>(op, a, nblk, nthr, sm, st);
+    }
     DWF_CUDA(cudaGetLastError());
     count_launch();
 }

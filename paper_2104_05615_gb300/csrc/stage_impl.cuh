@@ -381,6 +381,22 @@ __device__ __forceinline__ void mma_16816(float *d, const uint4 &a, uint32_t b0,
         : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void mma_1688(float *d, uint32_t a0, uint32_t a1, uint32_t b0)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+// Two 8x8 FP16 matrices, transposed: lanes 0..7 address the rows of the
+// first, 8..15 of the second (m16n8k8 B fragments of two n-tiles).
+__device__ __forceinline__ void ldmatrix_x2_trans(uint32_t addr, uint32_t &r0, uint32_t &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr));
+}
+
 // Four 8x8 FP16 matrices from shared memory, transposed: lane l supplies the
 // address of row (l & 7) of matrix (l >> 3); register i receives matrix i
 // with lane (g, t) holding rows 2t, 2t+1 of column g (an m16n8k16 B fragment).
@@ -436,7 +452,8 @@ struct StageSmem {
     int bar, nbr, smax, lraw, U, mat, col, scl, aux, auxs, dot, dots, H, A, D, total;
 };
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
-// Tensor-core operand tiles: FP16 [tile][chi][16 slices][kTcRow(TS) halfs],
+// Tensor-core operand tiles: FP16 [tile][chi][kt slices][kTcRow(TS) halfs]
+// (kt = 16, or 8 for Ls <= 8, whose products use m16n8k8),
 // one for h and one for aux; the row pitch is an odd number of 16-byte units
 // so the eight rows of an ldmatrix fall in distinct banks.
 __host__ __device__ constexpr int kTcRow(int TS) { return TS * 12 + 8; }
@@ -449,7 +466,7 @@ __host__ __device__ constexpr bool tc_alias(int TS, int Ls)
 }
 __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz, int rsz, bool tma,
                                                 bool tc, bool scale, bool has_aux, bool has_dot,
-                                                bool need_ha = true)
+                                                bool need_ha = true, int kt = 16)
 {
     // need_ha: the FP32 hop / aux buffers H, A (CUDA-core paths and the
     // bidiagonal S4); the tensor-core stages use the FP16 tiles instead
@@ -490,7 +507,7 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
         end = e > end ? e : end;
     }
     if (tc) {
-        const int bsz = (has_aux ? 2 : 1) * 2 * 16 * kTcRow(TS) * 2;
+        const int bsz = (has_aux ? 2 : 1) * 2 * kt * kTcRow(TS) * 2;
         const int db = TS * Ls * 24 * 4;
         int e;
         if (tc_alias(TS, Ls)) {
@@ -516,6 +533,8 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
     constexpr bool kTC = (T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8);
     constexpr bool kScale = (T::P == P16 || T::P == PFX16 || T::P == PFX8);
     constexpr bool kTma = kStage && (T::P != P64) && (kMode != MODE_5D);
+    // slices per tensor-core operand tile: Ls <= 8 (compile-time) uses 8
+    constexpr int KT = (LS > 0 && LS <= 8) ? 8 : 16;
     constexpr bool kAux = (kMode == MODE_S2 || kMode == MODE_S4);
     constexpr int NC = T::NC;
     // FP16 storage (values scaled to [-1, 1] per colour-spinor): projection and
@@ -544,7 +563,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
     const bool scale_bulk = kScale && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot, !kTC || kMode == MODE_S4);
+                                   has_dot, !kTC || kMode == MODE_S4, KT);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
     int *sN = reinterpret_cast<int *>(smem_raw + L.nbr);
     float *sMax = reinterpret_cast<float *>(smem_raw + L.smax);
@@ -950,10 +969,10 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         }
         {
             // slices Ls..15 of every tile are zero (K padded to 16)
-            const int padq = (16 - Ls) * RS / 8;
+            const int padq = (KT - Ls) * RS / 8;
             for (int e = tid; e < nk * 2 * padq; e += nthr) {
                 const int tl = e / padq, q = e - tl * padq;
-                reinterpret_cast<uint4 *>(sB + ((size_t)tl * 16 + Ls) * RS)[q] = make_uint4(0u, 0u, 0u, 0u);
+                reinterpret_cast<uint4 *>(sB + ((size_t)tl * KT + Ls) * RS)[q] = make_uint4(0u, 0u, 0u, 0u);
             }
         }
         __syncthreads();
@@ -964,7 +983,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             auto put = [&](__half *tile, const R *v) {
 #pragma unroll
                 for (int chi = 0; chi < 2; chi++) {
-                    uint2 *dst = reinterpret_cast<uint2 *>(tile + ((size_t)chi * 16 + s) * RS + jl * 12);
+                    uint2 *dst = reinterpret_cast<uint2 *>(tile + ((size_t)chi * KT + s) * RS + jl * 12);
 #pragma unroll
                     for (int q = 0; q < 3; q++) {
                         const R *w = v + chi * 12 + 4 * q;
@@ -974,7 +993,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             };
             // tile 0: aux (if any) else h ; tile 1: h
             if (kAux && !aux_tile) {
-                put(sB + (size_t)2 * 16 * RS, acc);
+                put(sB + (size_t)2 * KT * RS, acc);
             } else if constexpr (kAuxRaw) {
                 // stored halves times (aux scale / site scale) <= 1
                 const __half2 r2 = __float2half2_rn(asc * inv);
@@ -985,17 +1004,17 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 };
                 // chirality 0 = halves 0..11, chirality 1 = halves 12..23
                 uint2 *d0 = reinterpret_cast<uint2 *>(sB + (size_t)s * RS + jl * 12);
-                uint2 *d1 = reinterpret_cast<uint2 *>(sB + ((size_t)16 + s) * RS + jl * 12);
+                uint2 *d1 = reinterpret_cast<uint2 *>(sB + ((size_t)KT + s) * RS + jl * 12);
                 d0[0] = make_uint2(mul(araw[0].x), mul(araw[0].y));
                 d0[1] = make_uint2(mul(araw[0].z), mul(araw[0].w));
                 d0[2] = make_uint2(mul(araw[1].x), mul(araw[1].y));
                 d1[0] = make_uint2(mul(araw[1].z), mul(araw[1].w));
                 d1[1] = make_uint2(mul(araw[2].x), mul(araw[2].y));
                 d1[2] = make_uint2(mul(araw[2].z), mul(araw[2].w));
-                put(sB + (size_t)2 * 16 * RS, acc);
+                put(sB + (size_t)2 * KT * RS, acc);
             } else if (kAux) {
                 put(sB, av);
-                put(sB + (size_t)2 * 16 * RS, acc);
+                put(sB + (size_t)2 * KT * RS, acc);
             } else {
                 put(sB, acc);
             }
@@ -1020,11 +1039,22 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 if (kAux && kk == 0 && !aux_tile) continue;  // aux all zero in this tile
                 // A fragment of this lane, [G | -F] of this chirality and k-step
                 const uint4 af = __ldg(Af + ((chi * 2 + kk) * 32 + lane));
-                const __half *tb = sB + ((size_t)(kk * 2 + chi) * 16 + lr) * RS + pr * 16 + ln;
-                uint32_t b0, b1, b2, b3;
-                ldmatrix_x4_trans(smem_u32(tb), b0, b1, b2, b3);
-                mma_16816(d, af, b0, b1);
-                mma_16816(d + 4, af, b2, b3);
+                if constexpr (KT == 8) {
+                    // K = 8 slices: the first two registers of the k16 fragment
+                    // are the m16n8k8 A fragment (columns 0..7)
+                    const __half *tb = sB + ((size_t)(kk * 2 + chi) * 8 + (lane & 7)) * RS + pr * 16 +
+                                       8 * ((lane >> 3) & 1);
+                    uint32_t b0, b1;
+                    ldmatrix_x2_trans(smem_u32(tb), b0, b1);
+                    mma_1688(d, af.x, af.y, b0);
+                    mma_1688(d + 4, af.x, af.y, b1);
+                } else {
+                    const __half *tb = sB + ((size_t)(kk * 2 + chi) * 16 + lr) * RS + pr * 16 + ln;
+                    uint32_t b0, b1, b2, b3;
+                    ldmatrix_x4_trans(smem_u32(tb), b0, b1, b2, b3);
+                    mma_16816(d, af, b0, b1);
+                    mma_16816(d + 4, af, b2, b3);
+                }
             }
         };
         auto unit_store = [&](int u, const float *d) {
@@ -1215,8 +1245,9 @@ static void launch_t(const StageArgs &a, cudaStream_t st)
     const int nthr = (TS * Ls + 31) / 32 * 32;
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
     const bool scale_bulk = (T::P == P16 || T::P == PFX16 || T::P == PFX8) && (Ls % 4 == 0);
+    constexpr int KT = (LS > 0 && LS <= 8) ? 8 : 16;
     const StageSmem L = stage_smem(TS, Ls, T::NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot, !kTC || kMode == MODE_S4);
+                                   has_dot, !kTC || kMode == MODE_S4, KT);
     static bool attr_set = false;
     if (!attr_set) {
         DWF_CUDA(cudaFuncSetAttribute(stage_kernel<T, kMode, kMphi, kStage, kDag, LS, TSC>,
