@@ -750,7 +750,7 @@ def main():
         res = []
         for kind, op, prec in ((1, B.DWF_OP_LOCAL_DDAGD, cfg.get("inner_prec", "f32")),
                                (0, B.DWF_OP_DDAGD, "f32")):
-            for gather in (0, 1):
+            for gather in (0, 1, 2):
                 for tile in (4, 8, 16, 32):
                     try:
                         B.dwf_set_kernel_config(lat.h, PREC[prec], kind, tile, gather)

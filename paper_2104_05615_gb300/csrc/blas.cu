@@ -691,80 +691,111 @@ void launch_scalar(ScalarOp op, const ScalarArgs &a, cudaStream_t st)
 }
 
 // ------------------------------------------------------ reduced-Ls transform
-// out[(s,a)] = sum_{t,b} T[(s,a),(t,b)] in[(t,b)] per site and colour (dagger:
-// conj(T)^T), then optionally out += add_coef * addv.  T complex float,
-// (4 Ls_hat) x (4 Ls) row-major, as float pairs.
-__global__ void __launch_bounds__(512) tapply_kernel(Prec pout, void *out, int Ls_out, Prec pin,
-                                                     const void *in, int Ls_in, const float *T,
-                                                     long nsite, int dagger, const void *addv,
-                                                     Prec padd, double add_coef, int tile)
+// out[(s,a)] = sum_{t,b} E[(s,a),(t,b)] in[(t,b)] per site and colour, with
+// E = T (dagger = 0: Ls_in = 4 Ls columns of T, out at Ls_hat) or E = T^+
+// (dagger = 1), then optionally out += add_coef * addv.  T complex float,
+// (4 Ls_hat) x (4 Ls) row-major, as float pairs; arithmetic in FP32.
+//
+// Persistent CTAs: each stages E once, as [t][b][s][a] complex so that a
+// thread's four output spins are contiguous, then walks tiles of sites: the
+// tile's input columns go to shared memory and thread (site, s) accumulates
+// its 4 spins x 3 colours, each input entry (t, b) read once and used for
+// 48 fused multiply-adds.
+constexpr int kTapplyThreads = 256;
+
+__global__ void __launch_bounds__(kTapplyThreads) tapply_kernel(Prec pout, void *out, int Ls_out, Prec pin,
+                                                                const void *in, int Ls_in, const float *T,
+                                                                long nsite, int dagger, const void *addv,
+                                                                Prec padd, double add_coef, int tile)
 {
     extern __shared__ __align__(16) float sm_t[];
-    const int ncol = 4 * (dagger ? Ls_out : Ls_in);   // columns of T (4 Ls)
-    const int nrow = 4 * (dagger ? Ls_in : Ls_out);   // rows of T (4 Ls_hat)
-    float *sT = sm_t;                                   // [nrow][ncol][2]
-    float *sIn = sT + 2 * nrow * ncol;                  // [tile][Ls_in][24]
-    for (int e = threadIdx.x; e < 2 * nrow * ncol; e += blockDim.x) sT[e] = T[e];
-    // stage the input columns of the CTA's sites
-    for (int e = threadIdx.x; e < tile * Ls_in; e += blockDim.x) {
-        const int j = e / Ls_in, t = e - j * Ls_in;
-        const long site = (long)blockIdx.x * tile + j;
-        float v[24];
-        if (site < nsite) load_any<float>(pin, in, nsite, site, t, Ls_in, v);
-        else for (int r = 0; r < 24; r++) v[r] = 0;
-        for (int r = 0; r < 24; r++) sIn[(j * Ls_in + t) * 24 + r] = v[r];
+    float2 *sE = reinterpret_cast<float2 *>(sm_t);           // [4 Ls_in][Ls_out][4]
+    float *sIn = sm_t + 2 * 16 * Ls_in * Ls_out;              // [tile][Ls_in][24]
+    const int nin = 4 * Ls_in, nout = 4 * Ls_out;
+    const int ncolT = dagger ? nout : nin;                    // columns of T (4 Ls)
+    for (int e = threadIdx.x; e < nin * nout; e += blockDim.x) {
+        const int tb = e / nout, sa = e - tb * nout;
+        // E[(s,a),(t,b)]: T[sa][tb], or conj(T[tb][sa]) for T^+
+        float2 v;
+        if (!dagger) v = make_float2(T[2 * (sa * ncolT + tb)], T[2 * (sa * ncolT + tb) + 1]);
+        else v = make_float2(T[2 * (tb * ncolT + sa)], -T[2 * (tb * ncolT + sa) + 1]);
+        sE[e] = v;  // e = tb * nout + (s * 4 + a)
     }
-    __syncthreads();
     const int jl = threadIdx.x / Ls_out, s = threadIdx.x - jl * Ls_out;
-    const long i = (long)blockIdx.x * tile + jl;
-    if (jl >= tile || i >= nsite) return;
-    float o[24];
-    for (int r = 0; r < 24; r++) o[r] = 0;
-    const float *x = sIn + jl * Ls_in * 24;
-    for (int a = 0; a < 4; a++) {
-        const int row = s * 4 + a;  // output index (s, a)
-        for (int t = 0; t < Ls_in; t++)
-            for (int b = 0; b < 4; b++) {
-                const int col = t * 4 + b;  // input index
-                float tr, ti;
-                if (!dagger) {
-                    tr = sT[(row * ncol + col) * 2];
-                    ti = sT[(row * ncol + col) * 2 + 1];
-                } else {
-                    tr = sT[(col * ncol + row) * 2];
-                    ti = -sT[(col * ncol + row) * 2 + 1];
-                }
-                const float *xv = x + t * 24 + b * 6;
+    const long ntile = (nsite + tile - 1) / tile;
+    for (long tl = blockIdx.x; tl < ntile; tl += gridDim.x) {
+        __syncthreads();  // E staged / the previous tile's inputs consumed
+        for (int e = threadIdx.x; e < tile * Ls_in; e += blockDim.x) {
+            const int j = e / Ls_in, t = e - j * Ls_in;
+            const long site = tl * tile + j;
+            float v[24];
+            if (site < nsite) load_any<float>(pin, in, nsite, site, t, Ls_in, v);
+            else
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float xr = xv[2 * c], xi = xv[2 * c + 1];
-                    o[(a * 3 + c) * 2] += tr * xr - ti * xi;
-                    o[(a * 3 + c) * 2 + 1] += tr * xi + ti * xr;
-                }
+                for (int r = 0; r < 24; r++) v[r] = 0.f;
+            float4 *dst = reinterpret_cast<float4 *>(sIn + (j * Ls_in + t) * 24);
+#pragma unroll
+            for (int q = 0; q < 6; q++) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        __syncthreads();
+        const long i = tl * tile + jl;
+        if (jl >= tile || i >= nsite) continue;
+        float o[24];
+#pragma unroll
+        for (int r = 0; r < 24; r++) o[r] = 0.f;
+        const float *x = sIn + jl * Ls_in * 24;
+        for (int t = 0; t < Ls_in; t++) {
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const float2 *xv = reinterpret_cast<const float2 *>(x + t * 24 + b * 6);
+                const float2 x0 = xv[0], x1 = xv[1], x2 = xv[2];
+                const float4 *ep = reinterpret_cast<const float4 *>(sE + ((t * 4 + b) * Ls_out + s) * 4);
+                const float4 e01 = ep[0], e23 = ep[1];
+                const float2 E[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
+                                     make_float2(e23.x, e23.y), make_float2(e23.z, e23.w)};
+                const float2 X[3] = {x0, x1, x2};
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        float *oc = o + (a * 3 + c) * 2;
+                        oc[0] = fmaf(E[a].x, X[c].x, fmaf(-E[a].y, X[c].y, oc[0]));
+                        oc[1] = fmaf(E[a].x, X[c].y, fmaf(E[a].y, X[c].x, oc[1]));
+                    }
             }
+        }
+        if (addv) {
+            float w[24];
+            load_any<float>(padd, addv, nsite, i, s, Ls_out, w);
+#pragma unroll
+            for (int r = 0; r < 24; r++) o[r] += (float)add_coef * w[r];
+        }
+        store_any<float>(pout, out, nsite, i, s, Ls_out, o);
     }
-    if (addv) {
-        float w[24];
-        load_any<float>(padd, addv, nsite, i, s, Ls_out, w);
-        for (int r = 0; r < 24; r++) o[r] += (float)add_coef * w[r];
-    }
-    store_any<float>(pout, out, nsite, i, s, Ls_out, o);
 }
 
 void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
                    const float *T, long nsite, int dagger, const void *addv, Prec padd,
                    double add_coef, cudaStream_t st)
 {
-    const int tile = 8;
-    const size_t smem = sizeof(float) * (2 * 16 * Ls_out * Ls_in + tile * Ls_in * 24);
+    if (nsite == 0) return;
+    const int tile = std::max(1, kTapplyThreads / Ls_out);
+    const size_t smem = sizeof(float) * (2 * 16 * (size_t)Ls_out * Ls_in + (size_t)tile * Ls_in * 24);
     static bool attr = false;
     if (!attr) {
         DWF_CUDA(cudaFuncSetAttribute(tapply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       200 * 1024));
         attr = true;
     }
-    tapply_kernel<<<(unsigned)((nsite + tile - 1) / tile), tile * Ls_out, smem, st>>>(
-        pout, out, Ls_out, pin, in, Ls_in, T, nsite, dagger, addv, padd, add_coef, tile);
+    if (smem > 200 * 1024) throw std::runtime_error("reduced-Ls transform: fifth extents too large");
+    int dev = 0, nsm = 0, per_sm = 0;
+    DWF_CUDA(cudaGetDevice(&dev));
+    DWF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tapply_kernel, tile * Ls_out, smem));
+    const long ntile = (nsite + tile - 1) / tile;
+    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>(ntile, (long)nsm * std::max(1, per_sm)));
+    tapply_kernel<<<grid, tile * Ls_out, smem, st>>>(pout, out, Ls_out, pin, in, Ls_in, T, nsite, dagger, addv,
+                                                    padd, add_coef, tile);
     DWF_CUDA(cudaGetLastError());
     count_launch();
 }
