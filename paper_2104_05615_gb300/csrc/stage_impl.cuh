@@ -508,7 +508,7 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     }
     if (tc) {
         const int bsz = (has_aux ? 2 : 1) * 2 * kt * kTcRow(TS) * 2;
-        const int db = TS * Ls * 24 * 4;
+        const int db = TS * Ls * 24 * 2;  // the FP16 result D
         int e;
         if (tc_alias(TS, Ls)) {
             e = align16(o + (bsz > db ? bsz : db));
@@ -1064,25 +1064,15 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             for (int h = 0; h < 2; h++) {
                 const int nd = pr * 16 + h * 8 + 2 * tg;
                 const int jd = nd / 12, rd = chi * 12 + (nd - jd * 12);
-                if constexpr (kScale) {
-                    // scaled formats: D is normalised by the site scale (which
-                    // goes into the stored scale), so it is kept as FP16
-                    __half *sDh = reinterpret_cast<__half *>(sD);
-                    if (g < Ls)
-                        *reinterpret_cast<uint32_t *>(sDh + (jd * Ls + g) * 24 + rd) =
-                            pack_h2(d[4 * h], d[4 * h + 1]);
-                    if (g + 8 < Ls)
-                        *reinterpret_cast<uint32_t *>(sDh + (jd * Ls + g + 8) * 24 + rd) =
-                            pack_h2(d[4 * h + 2], d[4 * h + 3]);
-                } else {
-                    const float sd = sMax[jd];
-                    if (g < Ls)
-                        *reinterpret_cast<float2 *>(sD + (jd * Ls + g) * 24 + rd) =
-                            make_float2(d[4 * h] * sd, d[4 * h + 1] * sd);
-                    if (g + 8 < Ls)
-                        *reinterpret_cast<float2 *>(sD + (jd * Ls + g + 8) * 24 + rd) =
-                            make_float2(d[4 * h + 2] * sd, d[4 * h + 3] * sd);
-                }
+                // D is normalised by the site scale (the scaled formats fold
+                // that scale into the stored one, BF16 multiplies it back when
+                // reading D), so it is kept as FP16
+                __half *sDh = reinterpret_cast<__half *>(sD);
+                if (g < Ls)
+                    *reinterpret_cast<uint32_t *>(sDh + (jd * Ls + g) * 24 + rd) = pack_h2(d[4 * h], d[4 * h + 1]);
+                if (g + 8 < Ls)
+                    *reinterpret_cast<uint32_t *>(sDh + (jd * Ls + g + 8) * 24 + rd) =
+                        pack_h2(d[4 * h + 2], d[4 * h + 3]);
             }
         };
         if (alias) {
@@ -1109,21 +1099,14 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         }
         __syncthreads();
         if (active) {
-            if constexpr (kScale) {
-                const uint4 *q4 = reinterpret_cast<const uint4 *>(reinterpret_cast<const __half *>(sD) +
-                                                                  (jl * Ls + s) * 24);
+            const uint4 *q4 = reinterpret_cast<const uint4 *>(reinterpret_cast<const __half *>(sD) +
+                                                              (jl * Ls + s) * 24);
 #pragma unroll
-                for (int c = 0; c < 3; c++) unpack8(q4[c], out + 8 * c, __half());
-            } else {
-                const float4 *q4 = reinterpret_cast<const float4 *>(sD + (jl * Ls + s) * 24);
+            for (int c = 0; c < 3; c++) unpack8(q4[c], out + 8 * c, __half());
+            if constexpr (!kScale) {
+                const float sd = sMax[jl];
 #pragma unroll
-                for (int c = 0; c < 6; c++) {
-                    float4 f = q4[c];
-                    out[4 * c] = f.x;
-                    out[4 * c + 1] = f.y;
-                    out[4 * c + 2] = f.z;
-                    out[4 * c + 3] = f.w;
-                }
+                for (int r = 0; r < 24; r++) out[r] *= sd;
             }
         }
     } else {
