@@ -190,3 +190,19 @@ def test_16bit_outer_iterations(orc, outer, mspcg):
                       inner_prec="f16", maxiter=20000)
     assert st["converged"] and st["reliable_updates"] >= 1
     assert o.true_residual(x.cpu().numpy(), b) <= 1e-10 * 1.01
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mspcg", [True, False])
+def test_check_every_skips_host_reads(orc, mspcg):
+    """check_every = 4: the host reads the residual (and decides reliable updates
+    and convergence) every fourth iteration only; the solve still reaches the
+    oracle-verified tol, with at most the 3 iterations a check can lag plus one."""
+    lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
+    bd = torch.from_numpy(b).cuda()
+    kw = dict(mspcg=mspcg, tol=1e-10, inner_prec="f16", inner_iters=6)
+    _, st1 = lat.solve(bd, **kw)
+    x4, st4 = lat.solve(bd, check_every=4, **kw)
+    assert st4["converged"] and o.true_residual(x4.cpu().numpy(), b) <= 1e-10 * 1.01
+    assert st4["outer_iters"] % 4 == 0  # convergence is seen at check points only
+    assert st4["outer_iters"] <= st1["outer_iters"] + 4
