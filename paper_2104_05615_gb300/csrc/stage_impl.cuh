@@ -39,6 +39,10 @@
 namespace dwf {
 
 constexpr int kLinkStride = 20;  // reals per staged link (18 used, 16-byte aligned)
+// reals per site of staged links: its 8 links plus a 16-byte skew, so that the
+// links of the (up to three) sites a warp covers fall in different banks
+constexpr int kSiteLinkStride = 8 * kLinkStride + 4;
+__host__ __device__ constexpr int link_slot(int e) { return (e >> 3) * kSiteLinkStride + (e & 7) * kLinkStride; }
 
 // ------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -313,9 +317,10 @@ __device__ __forceinline__ void decode_chunks(const uint4 *p, int cs, typename T
     }
 }
 
-// acc[r] (+)= coef * sum_t M[chi(r)][s][t] X[t][r]; MT[t][s] holds (chi0, chi1) pairs
+// acc[r] (+)= coef * sum_t M[chi(r)][s][t] X[t][r] (slice t at X + t * xs);
+// MT[t][s] holds (chi0, chi1) pairs
 template <typename R, bool kAdd>
-__device__ __forceinline__ void apply5(const R *MT, const R *X, int Ls, int s, R *acc, R coef)
+__device__ __forceinline__ void apply5(const R *MT, const R *X, int xs, int Ls, int s, R *acc, R coef)
 {
     if (!kAdd) {
 #pragma unroll
@@ -325,7 +330,7 @@ __device__ __forceinline__ void apply5(const R *MT, const R *X, int Ls, int s, R
     for (int t = 0; t < Ls; t++) {
         const R f0 = coef * MT[(t * Ls + s) * 2];
         const R f1 = coef * MT[(t * Ls + s) * 2 + 1];
-        const R *x = X + t * 24;
+        const R *x = X + t * xs;
         R xv[24];
         if constexpr (sizeof(R) == 4) {
             const float4 *q = reinterpret_cast<const float4 *>(x);
@@ -350,6 +355,38 @@ __device__ __forceinline__ void apply5(const R *MT, const R *X, int Ls, int s, R
         for (int r = 0; r < 12; r++) acc[r] += f0 * xv[r];
 #pragma unroll
         for (int r = 12; r < 24; r++) acc[r] += f1 * xv[r];
+    }
+}
+
+// Per-(site, s) staging of 24 reals in shared memory (the hop result H and
+// the aux column A of the CUDA-core and bidiagonal stages): slice stride an
+// odd number of 16-byte units (28 floats, 26 doubles) and a 16-byte skew per
+// site, so that neither the slices of one site nor the (up to three) sites of
+// a warp share banks.
+template <typename R> __host__ __device__ constexpr int slice_stride() { return sizeof(R) == 8 ? 26 : 28; }
+template <typename R> __host__ __device__ inline int site_stride(int Ls) { return Ls * slice_stride<R>() + 16 / (int)sizeof(R); }
+// Twelve reals from a 16-byte aligned address.
+template <typename R>
+__device__ __forceinline__ void load12(const R *p, R *v)
+{
+    if constexpr (sizeof(R) == 4) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float4 f = q[c];
+            v[4 * c] = f.x;
+            v[4 * c + 1] = f.y;
+            v[4 * c + 2] = f.z;
+            v[4 * c + 3] = f.w;
+        }
+    } else {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            const double2 f = q[c];
+            v[2 * c] = f.x;
+            v[2 * c + 1] = f.y;
+        }
     }
 }
 
@@ -482,7 +519,7 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     m.lraw = o;
     o = align16(o + (tma ? TS * 96 * esz : 0));
     m.U = o;
-    o = align16(o + TS * 8 * kLinkStride * rsz);
+    o = align16(o + TS * kSiteLinkStride * rsz);
     m.mat = o;
     o = align16(o + (tc ? 0 : 4 * Ls * Ls * rsz));
     m.aux = o;
@@ -495,7 +532,7 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     o = align16(o + ((tma && has_dot && scale) ? TS * Ls * 4 : 0));
     // neighbour columns; the hop result (H, A or the FP16 tiles) and the
     // tensor-core output alias them afterwards
-    const int hb = TS * Ls * 24 * rsz;
+    const int hb = TS * (Ls * (rsz == 8 ? 26 : 28) + 16 / rsz) * rsz;
     m.col = o;
     m.scl = align16(o + (tma ? TS * 8 * colb : 0));
     int end = align16(m.scl + ((tma && scale) ? TS * 8 * Ls * 4 : 0));
@@ -571,6 +608,8 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
     R *sX = reinterpret_cast<R *>(smem_raw + L.mat);
     R *sH = reinterpret_cast<R *>(smem_raw + L.H);
     R *sA = reinterpret_cast<R *>(smem_raw + L.A);
+    const int hsl = slice_stride<R>(), hsite = site_stride<R>(Ls);
+    auto hofs = [&](int j, int t) { return j * hsite + t * hsl; };
     const int colb = NC * Ls * 16;
     const uint4 *sCol = reinterpret_cast<const uint4 *>(smem_raw + L.col);
     const float *sScl = reinterpret_cast<const float *>(smem_raw + L.scl);
@@ -663,7 +702,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 else u[q] = (R)lr[q];
             }
             reconstruct_row2<R>(u);
-            R *dst = sU + e * kLinkStride;
+            R *dst = sU + link_slot(e);
 #pragma unroll
             for (int q = 0; q < 18; q++) dst[q] = u[q];
         }
@@ -686,14 +725,14 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 }
                 if constexpr (kH2) {
                     // each element as two half2: (re, re) and (-im, im)
-                    __half2 *dst = reinterpret_cast<__half2 *>(sU + e * kLinkStride);
+                    __half2 *dst = reinterpret_cast<__half2 *>(sU + link_slot(e));
 #pragma unroll
                     for (int q = 0; q < 9; q++) {
                         dst[2 * q] = __floats2half2_rn(u[2 * q], u[2 * q]);
                         dst[2 * q + 1] = __floats2half2_rn(-u[2 * q + 1], u[2 * q + 1]);
                     }
                 } else {
-                    R *dst = sU + e * kLinkStride;
+                    R *dst = sU + link_slot(e);
 #pragma unroll
                     for (int q = 0; q < 18; q++) dst[q] = u[q];
                 }
@@ -798,7 +837,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                 for (int c = 0; c < NC; c++) raw[c] = __ldg(gp + (size_t)c * Ls + s);
                 const float w = (e >= 0 ? scl[k] : -scl[k]) * inv_ref;
                 hop_dir_h2_acc<mu, SG>(reinterpret_cast<const __half2 *>(raw),
-                                       reinterpret_cast<const __half2 *>(sU + (jl * 8 + k) * kLinkStride),
+                                       reinterpret_cast<const __half2 *>(sU + link_slot(jl * 8 + k)),
                                        __float2half2_rn(w), acc2);
                 return;
             } else if constexpr (T::P == PFX8) {
@@ -854,7 +893,7 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             }
             R h[12], chi[12];
             project_ct<mu, SG, R, kFxB>(psi, e >= 0 ? sc : -sc, h);
-            su3_mul_half_smem<R>(sU + (jl * 8 + k) * kLinkStride, h, chi);
+            su3_mul_half_smem<R>(sU + link_slot(jl * 8 + k), h, chi);
             accumulate_ct<mu, SG, R>(chi, acc);
         };
         dir(std::integral_constant<int, 0>{});
@@ -921,8 +960,8 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         // (P^T v)_s = v_{s-1} on spins 0,1 and v_{s+1} on spins 2,3 (wrap
         // terms times -mass).  G null (the D^+ operator): out = aux + (b h + c P^T h)/2.
         if (active) {
-            store24(sH + (jl * Ls + s) * 24, acc);
-            store24(sA + (jl * Ls + s) * 24, av);
+            store24(sH + hofs(jl, s), acc);
+            store24(sA + hofs(jl, s), av);
         }
         __syncthreads();
         if (active) {
@@ -933,13 +972,17 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
             const R flo = s > 0 ? R(1) : -mass, fhi = s + 1 < Ls ? R(1) : -mass;
             // the thread's own slice from registers, the neighbouring slices' halves
             // from shared memory
-            const R *Hm = sH + (jl * Ls + sm) * 24, *Am = sA + (jl * Ls + sm) * 24;
-            const R *Hp = sH + (jl * Ls + sp) * 24, *Ap = sA + (jl * Ls + sp) * 24;
+            R Hm[12], Am[12], Hp[12], Ap[12];
+            load12(sH + hofs(jl, sm), Hm);
+            load12(sA + hofs(jl, sm), Am);
+            load12(sH + hofs(jl, sp) + 12, Hp);
+            load12(sA + hofs(jl, sp) + 12, Ap);
             const R bl = cB * flo, cl = hc * flo, bh = cB * fhi, ch = hc * fhi;
 #pragma unroll
             for (int r = 0; r < 12; r++) out[r] = cA * av[r] + bl * Am[r] + hb * acc[r] + cl * Hm[r];
 #pragma unroll
-            for (int r = 12; r < 24; r++) out[r] = cA * av[r] + bh * Ap[r] + hb * acc[r] + ch * Hp[r];
+            for (int r = 12; r < 24; r++)
+                out[r] = cA * av[r] + bh * Ap[r - 12] + hb * acc[r] + ch * Hp[r - 12];
         }
     } else if constexpr (kTC) {
         // ---------------------------------------------------------------
@@ -955,17 +998,32 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         // tile whose first site lies beyond it has no aux and skips that k-step
         const bool aux_tile = kAux && (kMode == MODE_S4 || (int)(i0 - (long)seg * a.seg_out) < a.aux_valid);
         __half *sB = reinterpret_cast<__half *>(smem_raw + L.H);
-        if (active) {
+        {
             float m = 0.f;
+            if (active) {
 #pragma unroll
-            for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(acc[r]));
-            if constexpr (kAuxRaw) {
-                m = fmaxf(m, asc);
-            } else if constexpr (kAux) {
+                for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(acc[r]));
+                if constexpr (kAuxRaw) {
+                    m = fmaxf(m, asc);
+                } else if constexpr (kAux) {
 #pragma unroll
-                for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(av[r]));
+                    for (int r = 0; r < 24; r++) m = fmaxf(m, fabsf(av[r]));
+                }
             }
-            atomicMax(reinterpret_cast<int *>(sMax + jl), __float_as_int(m));
+            // the lanes of one site are consecutive (at most 16 of them in a
+            // warp): a segmented maximum by shuffles leaves the site's maximum
+            // in its first lane, which alone updates the shared value (one
+            // atomic per site and warp instead of one per thread)
+            const int lane = tid & 31;
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1) {
+                const float o = __shfl_down_sync(0xffffffffu, m, off);
+                const int oj = __shfl_down_sync(0xffffffffu, jl, off);
+                if (lane + off < 32 && oj == jl) m = fmaxf(m, o);
+            }
+            const int jprev = __shfl_up_sync(0xffffffffu, jl, 1);
+            if (active && (lane == 0 || jprev != jl))
+                atomicMax(reinterpret_cast<int *>(sMax + jl), __float_as_int(m));
         }
         {
             // slices Ls..15 of every tile are zero (K padded to 16)
@@ -1116,8 +1174,8 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
         // (the structured programs read the per-system b, c, mass, A, B)
         const bool structured = LS > 0 && a.fprog != FP_DENSE && a.mphi != nullptr;
         if (active) {
-            store24(sH + (jl * Ls + s) * 24, acc);
-            if (kAux && (a.G || structured)) store24(sA + (jl * Ls + s) * 24, av);
+            store24(sH + hofs(jl, s), acc);
+            if (kAux && (a.G || structured)) store24(sA + hofs(jl, s), av);
         }
         __syncthreads();
         if constexpr (LS > 0) {
@@ -1132,45 +1190,45 @@ __global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == 
                     const bool up = r < 12;  // chirality 0: spins 0, 1
                     R x[LS];
 #pragma unroll
-                    for (int t = 0; t < LS; t++) x[t] = sH[(j * LS + t) * 24 + r];
+                    for (int t = 0; t < LS; t++) x[t] = sH[hofs(j, t) + r];
                     switch (a.fprog) {
                     case FP_M5I: m5_solve<R, LS>(x, up, A5, q, mass); break;
                     case FP_M5ID: m5_solve<R, LS>(x, !up, A5, q, mass); break;
                     default:  // FP_S2
                         m5_solve<R, LS>(x, up, A5, q, mass);
 #pragma unroll
-                        for (int t = 0; t < LS; t++) x[t] = sA[(j * LS + t) * 24 + r] - x[t];
+                        for (int t = 0; t < LS; t++) x[t] = sA[hofs(j, t) + r] - x[t];
                         m5_solve<R, LS>(x, !up, A5, q, mass);
                         break;
                     }
                     if (kMode == MODE_S2 && a.fprog != FP_S2) {
                         // G null: aux - F h
 #pragma unroll
-                        for (int t = 0; t < LS; t++) x[t] = sA[(j * LS + t) * 24 + r] - x[t];
+                        for (int t = 0; t < LS; t++) x[t] = sA[hofs(j, t) + r] - x[t];
                     }
 #pragma unroll
-                    for (int t = 0; t < LS; t++) sH[(j * LS + t) * 24 + r] = x[t];
+                    for (int t = 0; t < LS; t++) sH[hofs(j, t) + r] = x[t];
                 }
                 __syncthreads();
                 if (active) {
 #pragma unroll
-                    for (int r = 0; r < 24; r++) out[r] = sH[(jl * Ls + s) * 24 + r];
+                    for (int r = 0; r < 24; r++) out[r] = sH[hofs(jl, s) + r];
                 }
             }
         }
-        const R *Hsite = sH + jl * Ls * 24;
+        const R *Hsite = sH + hofs(jl, 0);
         if (active && !structured) {
             if (kMode == MODE_F || kMode == MODE_5D) {
-                apply5<R, false>(sF, Hsite, Ls, s, out, R(1));
+                apply5<R, false>(sF, Hsite, hsl, Ls, s, out, R(1));
             } else {
                 // MODE_S2: out = G aux - F' h  (F' = G F; G null: aux - F h)
                 if (a.G) {
-                    apply5<R, false>(sG, sA + jl * Ls * 24, Ls, s, out, R(1));
+                    apply5<R, false>(sG, sA + hofs(jl, 0), hsl, Ls, s, out, R(1));
                 } else {
 #pragma unroll
                     for (int r = 0; r < 24; r++) out[r] = av[r];
                 }
-                apply5<R, true>(sF, Hsite, Ls, s, out, R(-1));
+                apply5<R, true>(sF, Hsite, hsl, Ls, s, out, R(-1));
             }
         }
     }
