@@ -559,11 +559,30 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     return m;
 }
 
+// Launch bounds.  The 16-bit stages with precomputed M_phi input are held to
+// DWF_STAGE_REGS_16 registers: the occupancy gain outweighs the extra
+// rematerialisation (M_phi on load needs more live values and is not
+// bounded; FP32 and FP64 are not bounded).  With a compile-time launch shape
+// (Ls and tile fixed) the block size is exact, which also lets the compiler
+// schedule for it; shapes fixed only at run time declare 512 threads.
+#ifndef DWF_STAGE_REGS_16
+#define DWF_STAGE_REGS_16 64
+#endif
+template <class T, bool kMphi, int LS, int TSC>
+struct StageLaunch {
+    static constexpr bool kFixed = LS > 0 && TSC > 0;
+    static constexpr bool k16 = T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8;
+    static constexpr int kThreads = kFixed ? (TSC * LS + 31) / 32 * 32 : 512;
+    // blocks per SM such that each of the four 16384-register partitions
+    // holds its share of the warps at the register budget
+    static constexpr int kMinBlocks = !(k16 && !kMphi) ? 1
+                                      : kFixed ? (16384 / (32 * DWF_STAGE_REGS_16)) * 4 / (kThreads / 32)
+                                               : 65536 / (512 * DWF_STAGE_REGS_16);
+};
+
 template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS, int TSC>
-// 16-bit stages with precomputed M_phi input are held to 64 registers (two
-// 512-thread blocks' worth per SM): the occupancy gain outweighs the extra
-// rematerialisation.  (M_phi on load needs more live values.)
-__global__ void __launch_bounds__(512, ((T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8) && !kMphi) ? 2 : 1)
+__global__ void __launch_bounds__(StageLaunch<T, kMphi, LS, TSC>::kThreads,
+                                  StageLaunch<T, kMphi, LS, TSC>::kMinBlocks)
     stage_kernel(const StageArgs a)
 {
     using R = typename T::R;
@@ -1319,7 +1338,7 @@ static void dispatch_mode(StageMode mode, bool mphi, const StageArgs &a, cudaStr
 }
 
 // Per-precision entry: compile-time fifth extent for Ls in {4, 8, 12, 16}
-// with direct gathers, and a compile-time 8-site tile for Ls 12 and 16 (the
+// with direct gathers, and a compile-time 8-site tile for Ls 8, 12 and 16 (the
 // tile the autotuner picks on GB300); every other case (and bulk-copy
 // gathers) uses the runtime-Ls, runtime-tile kernel.
 template <class T>
@@ -1341,7 +1360,10 @@ void launch_stage_prec(StageMode mode, bool mphi, const StageArgs &a, cudaStream
     } else {
         switch (a.Ls) {
         case 4: dispatch_mode<T, false, 4, 0>(mode, mphi, a, st); break;
-        case 8: dispatch_mode<T, false, 8, 0>(mode, mphi, a, st); break;
+        case 8:
+            if (a.tile == 8) dispatch_mode<T, false, 8, 8>(mode, mphi, a, st);
+            else dispatch_mode<T, false, 8, 0>(mode, mphi, a, st);
+            break;
         case 12:
             if (a.tile == 8) dispatch_mode<T, false, 12, 8>(mode, mphi, a, st);
             else dispatch_mode<T, false, 12, 0>(mode, mphi, a, st);
