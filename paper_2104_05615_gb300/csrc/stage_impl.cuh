@@ -503,10 +503,11 @@ __host__ __device__ constexpr bool tc_alias(int TS, int Ls)
 }
 __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz, int rsz, bool tma,
                                                 bool tc, bool scale, bool has_aux, bool has_dot,
-                                                bool need_ha = true, int kt = 16)
+                                                bool need_ha = true, int kt = 16, bool need_a = true)
 {
     // need_ha: the FP32 hop / aux buffers H, A (CUDA-core paths and the
-    // bidiagonal S4); the tensor-core stages use the FP16 tiles instead
+    // bidiagonal S4, which stages one combined buffer: need_a false); the
+    // tensor-core stages use the FP16 tiles instead
     StageSmem m;
     const int colb = NC * Ls * 16;
     int o = 0;
@@ -540,7 +541,7 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     m.A = align16(m.H + hb);
     m.D = o;
     if (need_ha) {
-        const int e = align16(m.A + (has_aux ? hb : 0));
+        const int e = align16(m.A + ((has_aux && need_a) ? hb : 0));
         end = e > end ? e : end;
     }
     if (tc) {
@@ -559,30 +560,47 @@ __host__ __device__ inline StageSmem stage_smem(int TS, int Ls, int NC, int esz,
     return m;
 }
 
-// Launch bounds.  The 16-bit stages with precomputed M_phi input are held to
-// DWF_STAGE_REGS_16 registers: the occupancy gain outweighs the extra
-// rematerialisation (M_phi on load needs more live values and is not
-// bounded; FP32 and FP64 are not bounded).  With a compile-time launch shape
-// (Ls and tile fixed) the block size is exact, which also lets the compiler
-// schedule for it; shapes fixed only at run time declare 512 threads.
+// Launch bounds.  The stages are latency-bound on their neighbour gathers,
+// so resident warps count for more than the rematerialisation a tight
+// register budget costs (measured on GB300).  With precomputed M_phi input:
+// FP16 stages of a compile-time shape 56 registers (S4, which keeps more
+// values live, 64), the other 16-bit and 8-bit stages 64, FP32 stages of a
+// compile-time shape 72.  M_phi on load needs more live values and is not
+// bounded, nor is FP64.  With a compile-time launch shape (Ls and tile fixed)
+// the block size is exact; shapes fixed only at run time declare 512 threads.
+#ifndef DWF_STAGE_REGS_F16
+#define DWF_STAGE_REGS_F16 56
+#endif
+#ifndef DWF_STAGE_REGS_F16_S4
+#define DWF_STAGE_REGS_F16_S4 64
+#endif
 #ifndef DWF_STAGE_REGS_16
 #define DWF_STAGE_REGS_16 64
 #endif
-template <class T, bool kMphi, int LS, int TSC>
+#ifndef DWF_STAGE_REGS_32
+#define DWF_STAGE_REGS_32 72
+#endif
+template <class T, int kMode, bool kMphi, int LS, int TSC>
 struct StageLaunch {
     static constexpr bool kFixed = LS > 0 && TSC > 0;
     static constexpr bool k16 = T::P == P16 || T::P == PB16 || T::P == PFX16 || T::P == PFX8;
     static constexpr int kThreads = kFixed ? (TSC * LS + 31) / 32 * 32 : 512;
+    static constexpr int kRegs = kMphi                       ? 0
+                                 : (T::P == P16 && kFixed)    ? (kMode == MODE_S4 ? DWF_STAGE_REGS_F16_S4
+                                                                                  : DWF_STAGE_REGS_F16)
+                                 : k16                        ? DWF_STAGE_REGS_16
+                                 : (T::P == P32 && kFixed)    ? DWF_STAGE_REGS_32
+                                                              : 0;
     // blocks per SM such that each of the four 16384-register partitions
     // holds its share of the warps at the register budget
-    static constexpr int kMinBlocks = !(k16 && !kMphi) ? 1
-                                      : kFixed ? (16384 / (32 * DWF_STAGE_REGS_16)) * 4 / (kThreads / 32)
-                                               : 65536 / (512 * DWF_STAGE_REGS_16);
+    static constexpr int kMinBlocks = kRegs == 0 ? 1
+                                      : kFixed ? (16384 / (32 * kRegs)) * 4 / (kThreads / 32)
+                                               : 65536 / (512 * kRegs);
 };
 
 template <class T, int kMode, bool kMphi, bool kStage, bool kDag, int LS, int TSC>
-__global__ void __launch_bounds__(StageLaunch<T, kMphi, LS, TSC>::kThreads,
-                                  StageLaunch<T, kMphi, LS, TSC>::kMinBlocks)
+__global__ void __launch_bounds__(StageLaunch<T, kMode, kMphi, LS, TSC>::kThreads,
+                                  StageLaunch<T, kMode, kMphi, LS, TSC>::kMinBlocks)
     stage_kernel(const StageArgs a)
 {
     using R = typename T::R;
@@ -619,7 +637,7 @@ __global__ void __launch_bounds__(StageLaunch<T, kMphi, LS, TSC>::kThreads,
     const bool has_dot = (kMode == MODE_S4) && a.dot_part;
     const bool scale_bulk = kScale && (Ls % 4 == 0);
     const StageSmem L = stage_smem(TS, Ls, NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot, !kTC || kMode == MODE_S4, KT);
+                                   has_dot, !kTC || kMode == MODE_S4, KT, kMode != MODE_S4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
     int *sN = reinterpret_cast<int *>(smem_raw + L.nbr);
     float *sMax = reinterpret_cast<float *>(smem_raw + L.smax);
@@ -978,30 +996,31 @@ __global__ void __launch_bounds__(StageLaunch<T, kMphi, LS, TSC>::kThreads,
         // chirality: out = A aux + B P^T aux + (b h + c P^T h) / 2, where
         // (P^T v)_s = v_{s-1} on spins 0,1 and v_{s+1} on spins 2,3 (wrap
         // terms times -mass).  G null (the D^+ operator): out = aux + (b h + c P^T h)/2.
+        // The shifted terms share one factor per slice (1, or -mass on the
+        // wrap), so each (site, s) stages q = B aux + (c/2) h once and reads
+        // the neighbouring slices' halves of q.
+        const double *mp = a.mphi + 5 * sys;
+        const R hb = (R)(0.5 * mp[0]), hc = (R)(0.5 * mp[1]), mass = (R)mp[2];
+        const R cA = a.G ? (R)mp[3] : R(1), cB = a.G ? (R)mp[4] : R(0);
         if (active) {
-            store24(sH + hofs(jl, s), acc);
-            store24(sA + hofs(jl, s), av);
+            R q[24];
+#pragma unroll
+            for (int r = 0; r < 24; r++) q[r] = cB * av[r] + hc * acc[r];
+            store24(sH + hofs(jl, s), q);
         }
         __syncthreads();
         if (active) {
-            const double *mp = a.mphi + 5 * sys;
-            const R hb = (R)(0.5 * mp[0]), hc = (R)(0.5 * mp[1]), mass = (R)mp[2];
-            const R cA = a.G ? (R)mp[3] : R(1), cB = a.G ? (R)mp[4] : R(0);
             const int sm = s > 0 ? s - 1 : Ls - 1, sp = s + 1 < Ls ? s + 1 : 0;
             const R flo = s > 0 ? R(1) : -mass, fhi = s + 1 < Ls ? R(1) : -mass;
-            // the thread's own slice from registers, the neighbouring slices' halves
-            // from shared memory
-            R Hm[12], Am[12], Hp[12], Ap[12];
-            load12(sH + hofs(jl, sm), Hm);
-            load12(sA + hofs(jl, sm), Am);
-            load12(sH + hofs(jl, sp) + 12, Hp);
-            load12(sA + hofs(jl, sp) + 12, Ap);
-            const R bl = cB * flo, cl = hc * flo, bh = cB * fhi, ch = hc * fhi;
+            // the thread's own slice from registers, the neighbouring slices'
+            // halves from shared memory
+            R Qm[12], Qp[12];
+            load12(sH + hofs(jl, sm), Qm);
+            load12(sH + hofs(jl, sp) + 12, Qp);
 #pragma unroll
-            for (int r = 0; r < 12; r++) out[r] = cA * av[r] + bl * Am[r] + hb * acc[r] + cl * Hm[r];
+            for (int r = 0; r < 12; r++) out[r] = cA * av[r] + hb * acc[r] + flo * Qm[r];
 #pragma unroll
-            for (int r = 12; r < 24; r++)
-                out[r] = cA * av[r] + bh * Ap[r - 12] + hb * acc[r] + ch * Hp[r - 12];
+            for (int r = 12; r < 24; r++) out[r] = cA * av[r] + hb * acc[r] + fhi * Qp[r - 12];
         }
     } else if constexpr (kTC) {
         // ---------------------------------------------------------------
@@ -1307,7 +1326,7 @@ static void launch_t(const StageArgs &a, cudaStream_t st)
     const bool scale_bulk = (T::P == P16 || T::P == PFX16 || T::P == PFX8) && (Ls % 4 == 0);
     constexpr int KT = (LS > 0 && LS <= 8) ? 8 : 16;
     const StageSmem L = stage_smem(TS, Ls, T::NC, sizeof(LE), sizeof(R), kTma, kTC, scale_bulk, kAux,
-                                   has_dot, !kTC || kMode == MODE_S4, KT);
+                                   has_dot, !kTC || kMode == MODE_S4, KT, kMode != MODE_S4);
     static bool attr_set = false;
     if (!attr_set) {
         DWF_CUDA(cudaFuncSetAttribute(stage_kernel<T, kMode, kMphi, kStage, kDag, LS, TSC>,
