@@ -774,11 +774,182 @@ __global__ void __launch_bounds__(kTapplyThreads) tapply_kernel(Prec pout, void 
     }
 }
 
+// Tensor-core form of the same transform, for inner storage of BF16 precision
+// or coarser.  Per site and colour the map is a real product: rows (colour,
+// site), K = (t, b, re/im) = 8 Ls_in, N = (s, a, re/im) = 8 Ls_out, with each
+// complex E entry expanded to the real block [[Er, -Ei], [Ei, Er]].  BF16
+// operands (about three significant digits, like the storage the transform
+// feeds or reads), FP32 accumulation, mma.sync m16n8k16.  Persistent CTAs of
+// four warps stage the expanded E once as [n][k]; each tile of 16 sites is
+// staged as the 48 x K operand [colour * 16 + site][k], multiplied (warp w
+// takes n-tiles w, w + 4, ..., n-tile = output slice s), and written back per
+// (site, s) through a shared FP32 buffer (the output formats with a scale per
+// (site, s) need the whole colour-spinor).
+constexpr int kTtcSites = 16;
+constexpr int kTtcThreads = 128;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16_16816(float *d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Shared memory of the tensor-core transform (bytes): E [N][K + 8] and the
+// operand [48][K + 8] in BF16 (row pitch an odd number of 16-byte units for
+// even Ls_in, so ldmatrix is conflict-free), the result [16][Ls_out][24] FP32.
+__host__ __device__ inline size_t ttc_smem(int Ls_in, int Ls_out)
+{
+    const size_t kp = 8 * (size_t)Ls_in + 8;
+    return 2 * kp * (8 * (size_t)Ls_out + 3 * kTtcSites) + 4 * (size_t)kTtcSites * Ls_out * 24;
+}
+
+__global__ void __launch_bounds__(kTtcThreads) tapply_tc_kernel(Prec pout, void *out, int Ls_out, Prec pin,
+                                                                const void *in, int Ls_in, const float *T,
+                                                                long nsite, int dagger, const void *addv,
+                                                                Prec padd, double add_coef)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int K = 8 * Ls_in, N = 8 * Ls_out, KP = K + 8;
+    __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(sm_raw);  // [N][KP]
+    __nv_bfloat16 *sA = sW + (size_t)N * KP;                            // [48][KP]
+    float *sC = reinterpret_cast<float *>(sA + (size_t)3 * kTtcSites * KP);  // [16][Ls_out][24]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncolT = 4 * (dagger ? Ls_out : Ls_in);  // columns of T (4 Ls)
+    for (int e = tid; e < N * K; e += kTtcThreads) {
+        const int n = e / K, k = e - n * K;
+        const int sa = n >> 1, ro = n & 1, tb = k >> 1, ri = k & 1;
+        // E[(s,a),(t,b)]: T[sa][tb], or conj(T[tb][sa]) for T^+
+        float er, ei;
+        if (!dagger) {
+            er = T[2 * (sa * ncolT + tb)];
+            ei = T[2 * (sa * ncolT + tb) + 1];
+        } else {
+            er = T[2 * (tb * ncolT + sa)];
+            ei = -T[2 * (tb * ncolT + sa) + 1];
+        }
+        const float w = ro == 0 ? (ri == 0 ? er : -ei) : (ri == 0 ? ei : er);
+        sW[(size_t)n * KP + k] = __float2bfloat16_rn(w);
+    }
+    const int g = lane >> 2, tg = lane & 3;
+    const long ntile = (nsite + kTtcSites - 1) / kTtcSites;
+    for (long tl = blockIdx.x; tl < ntile; tl += gridDim.x) {
+        __syncthreads();  // E staged / the previous tile's operand and result consumed
+        // operand rows (colour c, site j), k = (t * 4 + b) * 2 + re/im
+        for (int e = tid; e < kTtcSites * Ls_in; e += kTtcThreads) {
+            const int j = e / Ls_in, t = e - j * Ls_in;
+            const long site = tl * kTtcSites + j;
+            float v[24];
+            if (site < nsite) load_any<float>(pin, in, nsite, site, t, Ls_in, v);
+            else
+#pragma unroll
+                for (int r = 0; r < 24; r++) v[r] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 12; q++) {  // component pair q = b * 3 + c: (re, im)
+                const int b = q / 3, c = q - 3 * b;
+                *reinterpret_cast<uint32_t *>(sA + (size_t)(c * kTtcSites + j) * KP + (t * 4 + b) * 2) =
+                    pack_bf2(v[2 * q], v[2 * q + 1]);
+            }
+        }
+        __syncthreads();
+        for (int nt = warp; nt < Ls_out; nt += kTtcThreads / 32) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int ks = 0; ks < K; ks += 16) {
+                    uint32_t a0, a1, a2, a3, b0, b1;
+                    const __nv_bfloat16 *pa =
+                        sA + (size_t)(c * kTtcSites + (lane & 7) + 8 * ((lane >> 3) & 1)) * KP + ks + 8 * (lane >> 4);
+                    ldsm_x4(smem_addr(pa), a0, a1, a2, a3);
+                    const __nv_bfloat16 *pb = sW + (size_t)(nt * 8 + (lane & 7)) * KP + ks + 8 * ((lane >> 3) & 1);
+                    ldsm_x2(smem_addr(pb), b0, b1);
+                    mma_bf16_16816(d, a0, a1, a2, a3, b0, b1);
+                }
+                // rows g, g + 8 = sites; columns 2 tg, 2 tg + 1 = (s = nt, a = tg, re / im)
+                float2 *c0 = reinterpret_cast<float2 *>(sC + ((size_t)g * Ls_out + nt) * 24 + (tg * 3 + c) * 2);
+                float2 *c1 = reinterpret_cast<float2 *>(sC + ((size_t)(g + 8) * Ls_out + nt) * 24 + (tg * 3 + c) * 2);
+                *c0 = make_float2(d[0], d[1]);
+                *c1 = make_float2(d[2], d[3]);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < kTtcSites * Ls_out; e += kTtcThreads) {
+            const int j = e / Ls_out, s = e - j * Ls_out;
+            const long site = tl * kTtcSites + j;
+            if (site >= nsite) continue;
+            float o[24];
+            const float4 *src = reinterpret_cast<const float4 *>(sC + (size_t)e * 24);
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                const float4 f = src[q];
+                o[4 * q] = f.x;
+                o[4 * q + 1] = f.y;
+                o[4 * q + 2] = f.z;
+                o[4 * q + 3] = f.w;
+            }
+            if (addv) {
+                float w[24];
+                load_any<float>(padd, addv, nsite, site, s, Ls_out, w);
+#pragma unroll
+                for (int r = 0; r < 24; r++) o[r] += (float)add_coef * w[r];
+            }
+            store_any<float>(pout, out, nsite, site, s, Ls_out, o);
+        }
+    }
+}
+
+static bool launch_tapply_tc(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
+                             const float *T, long nsite, int dagger, const void *addv, Prec padd,
+                             double add_coef, cudaStream_t st)
+{
+    // K = 8 Ls_in must be a whole number of 16-wide k-steps
+    if (Ls_in % 2 != 0 || Ls_in > 16 || Ls_out > 16) return false;
+    const size_t smem = ttc_smem(Ls_in, Ls_out);
+    static bool attr = false;
+    if (!attr) {
+        DWF_CUDA(cudaFuncSetAttribute(tapply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    DWF_CUDA(cudaGetDevice(&dev));
+    DWF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tapply_tc_kernel, kTtcThreads, smem));
+    const long ntile = (nsite + kTtcSites - 1) / kTtcSites;
+    const unsigned grid = (unsigned)std::max<long>(1, std::min<long>(ntile, (long)nsm * std::max(1, per_sm)));
+    tapply_tc_kernel<<<grid, kTtcThreads, smem, st>>>(pout, out, Ls_out, pin, in, Ls_in, T, nsite, dagger, addv,
+                                                       padd, add_coef);
+    DWF_CUDA(cudaGetLastError());
+    count_launch();
+    return true;
+}
+
 void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
                    const float *T, long nsite, int dagger, const void *addv, Prec padd,
-                   double add_coef, cudaStream_t st)
+                   double add_coef, cudaStream_t st, bool tensor_cores)
 {
     if (nsite == 0) return;
+    if (tensor_cores &&
+        launch_tapply_tc(pout, out, Ls_out, pin, in, Ls_in, T, nsite, dagger, addv, padd, add_coef, st))
+        return;
     const int tile = std::max(1, kTapplyThreads / Ls_out);
     const size_t smem = sizeof(float) * (2 * 16 * (size_t)Ls_out * Ls_in + (size_t)tile * Ls_in * 24);
     static bool attr = false;

@@ -173,9 +173,11 @@ struct ScalarArgs {
 void launch_scalar(ScalarOp op, const ScalarArgs &a, cudaStream_t st);
 
 // Fifth-dimension transform (reduced Ls): out[(s,a)] = sum T[(s,a),(t,b)] in[(t,b)]
+// tensor_cores: BF16 operands with FP32 accumulation (for inner storage of
+// BF16 precision or coarser; even Ls_in), else FP32 on the CUDA cores.
 void launch_tapply(Prec pout, void *out, int Ls_out, Prec pin, const void *in, int Ls_in,
                    const float *T, long nsite, int dagger, const void *addv, Prec padd,
-                   double add_coef, cudaStream_t st);
+                   double add_coef, cudaStream_t st, bool tensor_cores = false);
 // G (device, (4 La) x (4 Lb) complex) = sum over sites and colours of a b^+
 // for canonical FP64 fields; work: tcontract_workspace_bytes(La, Lb) bytes.
 size_t tcontract_workspace_bytes(int La, int Lb);

@@ -84,7 +84,31 @@ def test_reduced_ls_preconditioner_matches_oracle(orc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("inner", ["bf16", "fx16"])
+@pytest.mark.parametrize("inner,tol", [("bf16", 2e-2), ("fx8", 6e-2)])
+def test_reduced_ls_preconditioner_tensor_core_transform(orc, inner, tol):
+    """With BF16 or 8-bit inner storage the maps T and T^+ run on the tensor
+    cores with BF16 operands (FP32 accumulation).  Against the FP64 oracle's
+    reduced-Ls preconditioner with a dense T: the bound is a few roundings
+    of the inner storage (BF16 2^-9, 8-bit fixed point 2^-8 of the site
+    scale per element) carried through two inner iterations, far below the
+    O(1) error of a misplaced operand row or column."""
+    from paper_2104_05615_gb300 import binding as B
+    from paper_2104_05615_gb300.lattice import heuristic_T, PREC
+    lat, o, r = make(orc, (8, 4, 4, 4), 8, (4, 4, 4, 4), 0.05, 0.5)
+    rng = np.random.default_rng(4)
+    T = heuristic_T(8, 4) + 0.2 * (rng.standard_normal((16, 32)) + 1j * rng.standard_normal((16, 32)))
+    lat.set_reduced_ls(4, T, 0.3)
+    rd = torch.from_numpy(r).cuda()
+    z = torch.empty_like(rd)
+    B.dwf_precondition(lat.h, z, rd, B.default_params(inner_prec=PREC[inner], inner_iters=2,
+                                                       use_reduced_ls=1))
+    zr = o.precond(r, orc.PREC_REDUCED, k=2, sub=(4, 4, 4, 4), Ls_hat=4, T=T, mu=0.3)
+    e = np.linalg.norm(z.cpu().numpy() - zr) / np.linalg.norm(zr)
+    assert e < tol, e
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("inner", ["bf16", "fx16", "fx8"])
 def test_mspcg_reduced_ls_converges(orc, inner):
     from paper_2104_05615_gb300.lattice import heuristic_T
     lat, o, b = make(orc, (8, 8, 4, 4), 8, (4, 4, 4, 4), 0.01, 0.5)
