@@ -774,17 +774,18 @@ __global__ void __launch_bounds__(kTapplyThreads) tapply_kernel(Prec pout, void 
     }
 }
 
-// Tensor-core form of the same transform, for inner storage of BF16 precision
-// or coarser.  Per site and colour the map is a real product: rows (colour,
+// Tensor-core form of the same transform, for an output stored in BF16
+// precision or coarser (the forward map r -> T r into BF16 or 8-bit inner
+// storage).  Per site and colour the map is a real product: rows (colour,
 // site), K = (t, b, re/im) = 8 Ls_in, N = (s, a, re/im) = 8 Ls_out, with each
 // complex E entry expanded to the real block [[Er, -Ei], [Ei, Er]].  BF16
-// operands (about three significant digits, like the storage the transform
-// feeds or reads), FP32 accumulation, mma.sync m16n8k16.  Persistent CTAs of
-// four warps stage the expanded E once as [n][k]; each tile of 16 sites is
-// staged as the 48 x K operand [colour * 16 + site][k], multiplied (warp w
-// takes n-tiles w, w + 4, ..., n-tile = output slice s), and written back per
-// (site, s) through a shared FP32 buffer (the output formats with a scale per
-// (site, s) need the whole colour-spinor).
+// operands (the input rounded to the precision of the storage it feeds),
+// FP32 accumulation, mma.sync m16n8k16.  Persistent CTAs of four warps stage
+// the expanded E once as [n][k]; each tile of 16 sites is staged as the
+// 48 x K operand [colour * 16 + site][k], multiplied (warp w takes n-tiles
+// w, w + 4, ..., n-tile = output slice s), and written back per (site, s)
+// through a shared FP32 buffer (the output formats with a scale per (site, s)
+// need the whole colour-spinor).
 constexpr int kTtcSites = 16;
 constexpr int kTtcThreads = 128;
 
@@ -877,11 +878,11 @@ __global__ void __launch_bounds__(kTtcThreads) tapply_tc_kernel(Prec pout, void 
                 float d[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int ks = 0; ks < K; ks += 16) {
                     uint32_t a0, a1, a2, a3, b0, b1;
+                    const __nv_bfloat16 *pb = sW + (size_t)(nt * 8 + (lane & 7)) * KP + ks + 8 * ((lane >> 3) & 1);
+                    ldsm_x2(smem_addr(pb), b0, b1);
                     const __nv_bfloat16 *pa =
                         sA + (size_t)(c * kTtcSites + (lane & 7) + 8 * ((lane >> 3) & 1)) * KP + ks + 8 * (lane >> 4);
                     ldsm_x4(smem_addr(pa), a0, a1, a2, a3);
-                    const __nv_bfloat16 *pb = sW + (size_t)(nt * 8 + (lane & 7)) * KP + ks + 8 * ((lane >> 3) & 1);
-                    ldsm_x2(smem_addr(pb), b0, b1);
                     mma_bf16_16816(d, a0, a1, a2, a3, b0, b1);
                 }
                 // rows g, g + 8 = sites; columns 2 tg, 2 tg + 1 = (s = nt, a = tg, re / im)
@@ -922,6 +923,8 @@ static bool launch_tapply_tc(Prec pout, void *out, int Ls_out, Prec pin, const v
                              double add_coef, cudaStream_t st)
 {
     // K = 8 Ls_in must be a whole number of 16-wide k-steps
+    // outputs of BF16 precision or coarser only
+    if (pout != PB16 && pout != PFX8) return false;
     if (Ls_in % 2 != 0 || Ls_in > 16 || Ls_out > 16) return false;
     const size_t smem = ttc_smem(Ls_in, Ls_out);
     static bool attr = false;

@@ -229,12 +229,12 @@ void precond_apply(Ctx &c, Prec po, const void *r, void *z, int &inner_count)
         const int L = E.Ls_hat;
         void *rin = E.ws("in_r", field_bytes(pi, n, L));
         void *zin = E.ws("in_z", field_bytes(P32, n, L));
-        // BF16 (or 8-bit) inner storage: the transform on the tensor cores with
-        // BF16 operands, whose rounding is that of the storage it feeds
-        const bool tc = pi == PB16 || pi == PFX8;
-        launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st, tc);
+        // into BF16 (or 8-bit) inner storage the forward map runs on the tensor
+        // cores with BF16 operands, the rounding of the storage it feeds; T^+
+        // (FP32 output) stays in FP32 on the CUDA cores
+        launch_tapply(pi, rin, L, po, r, E.Ls, E.Tm, n, 0, nullptr, P32, 0.0, c.st, true);
         inner_cg(c, L, rin, pi, zin, P32, P.inner_iters);
-        launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st, tc);
+        launch_tapply(po, z, E.Ls, P32, zin, L, E.Tm, n, 1, r, po, E.mu, c.st);
     } else {
         inner_cg(c, E.Ls, r, po, z, po, P.inner_iters);
     }

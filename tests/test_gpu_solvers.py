@@ -86,12 +86,14 @@ def test_reduced_ls_preconditioner_matches_oracle(orc):
 @pytest.mark.gpu
 @pytest.mark.parametrize("inner,tol", [("bf16", 2e-2), ("fx8", 6e-2)])
 def test_reduced_ls_preconditioner_tensor_core_transform(orc, inner, tol):
-    """With BF16 or 8-bit inner storage the maps T and T^+ run on the tensor
-    cores with BF16 operands (FP32 accumulation).  Against the FP64 oracle's
-    reduced-Ls preconditioner with a dense T: the bound is a few roundings
-    of the inner storage (BF16 2^-9, 8-bit fixed point 2^-8 of the site
-    scale per element) carried through two inner iterations, far below the
-    O(1) error of a misplaced operand row or column."""
+    """With BF16 or 8-bit inner storage the forward map r -> T r runs on the
+    tensor cores with BF16 operands and FP32 accumulation (input and T
+    rounded to BF16, the precision of the storage it feeds).  Against the
+    FP64 oracle's reduced-Ls preconditioner with a dense T: the bound is a
+    few roundings of the inner storage (BF16 2^-9, 8-bit fixed point 2^-8 of
+    the site scale per element) and of T carried through two inner
+    iterations, far below the O(1) error of a misplaced operand row or
+    column."""
     from paper_2104_05615_gb300 import binding as B
     from paper_2104_05615_gb300.lattice import heuristic_T, PREC
     lat, o, r = make(orc, (8, 4, 4, 4), 8, (4, 4, 4, 4), 0.05, 0.5)
